@@ -1,0 +1,238 @@
+/*
+ * diffus.h - C ABI of the GB300 DiffUS renderer (libdiffus.so).
+ *
+ * DiffUS (Bertramo, Duguey, Gopalakrishnan, arXiv 2508.06768) renders B-mode
+ * ultrasound images from an acoustic-impedance volume: fan-beam rays are
+ * marched through Z(x,y,z) (Section 2.3), every pair of consecutive samples
+ * forms an interface with the coefficients of Eq. 1, the coupled recurrences
+ * of Eq. 2 are solved as the sparse system of Eq. 3/4 for every truncation
+ * depth k (Section 2.4), the echo rows are the first differences of the
+ * returning amplitude d_0^(k), and speckle and a depth-dependent lateral blur
+ * are applied (Section 2.4).  The whole renderer is differentiable
+ * (Abstract, Section 1): this library also returns dL/dZ and dL/dpose.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers marked (device) are CUDA device pointers on the current
+ *    device; (host) pointers are ordinary host memory read during the call.
+ *  - The caller owns every buffer.  Device work runs asynchronously on the
+ *    given stream; no entry point synchronises, allocates or frees, so the
+ *    device-side calls can be captured in a CUDA graph.
+ *  - Return value: DIFFUS_OK (0) or a negative DIFFUS_E_* code for invalid
+ *    arguments or a failed launch; diffus_strerror() names it.  Invalid input
+ *    is rejected on the host before anything is launched.  Nothing traps.
+ *  - Volume: Z[nz][ny][nx] (x fastest), float32 or bfloat16, in MRayl, voxel
+ *    centres at origin + index * spacing (mm).  Every dimension >= 2.
+ *  - Pose: 6 float32 (device): translation t (mm) then ZYX Euler angles
+ *    (rx, ry, rz) in radians; R = Rz(rz) Ry(ry) Rx(rx) maps probe axes
+ *    (x lateral, y elevation, z axial) to volume axes.
+ *  - Fan: ray j has beam angle theta_j = -fov/2 + fov j/(n_rays-1) (0 for one
+ *    ray) and direction u_j = R (sin theta_j, 0, cos theta_j).  Sample k
+ *    (k = 0..S) lies at t + (k + 1/2) ds u_j with ds = depth/S; outside the
+ *    volume the coordinates are clamped to the border.
+ *  - Image: float32 [n_rays][S] row-major; row k of ray j is the echo
+ *    returned from depth (k+1) ds.
+ *  - Status (device, nullable): uint32[4], zeroed by each call then filled:
+ *      [0] rays that meet a pole of the depth system (see ray_valid),
+ *      [1] non-finite image values written,
+ *      [2] error bits (DIFFUS_STATUS_*),
+ *      [3] reserved (0).
+ */
+#ifndef DIFFUS_H
+#define DIFFUS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *diffus_stream_t;   /* cudaStream_t */
+
+enum {
+    DIFFUS_OK = 0,
+    DIFFUS_E_NULL = -1,        /* required pointer is NULL */
+    DIFFUS_E_DIMS = -2,        /* volume or fan sizes out of range */
+    DIFFUS_E_PARAM = -3,       /* a parameter is out of range or not finite */
+    DIFFUS_E_DTYPE = -4,       /* unsupported volume dtype */
+    DIFFUS_E_ALIGN = -5,       /* pointer not aligned for its element type */
+    DIFFUS_E_WORKSPACE = -6,   /* workspace missing or too small */
+    DIFFUS_E_LAUNCH = -7,      /* a CUDA launch or async call failed */
+    DIFFUS_E_PLAN = -8,        /* batch plan corrupt or for other inputs */
+    DIFFUS_E_DEVICE = -9       /* no usable CUDA device / wrong architecture */
+};
+
+enum { DIFFUS_F32 = 0, DIFFUS_BF16 = 1 };
+enum { DIFFUS_MODE_LITERAL = 0, DIFFUS_MODE_SIGNED = 1 };
+enum { DIFFUS_STATUS_QUEUE = 1u, DIFFUS_STATUS_PLAN = 2u };
+
+/* Volume geometry.  dtype is DIFFUS_F32 or DIFFUS_BF16. */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t dtype;
+    double sx, sy, sz;          /* spacing, mm (> 0) */
+    double ox, oy, oz;          /* centre of voxel (0,0,0), mm */
+} diffus_volume_desc;
+
+/* Fan-beam acquisition (Section 2.4, Section 3.1). */
+typedef struct {
+    int32_t n_rays;             /* >= 1 */
+    int32_t n_samples;          /* S >= 1; a ray carries S+1 samples, S echo rows */
+    double fov_rad;             /* in [0, pi) */
+    double depth_mm;            /* > 0 */
+    double f_mhz;               /* >= 0, centre frequency */
+    double alpha_db_cm_mhz;     /* >= 0, attenuation (uniform, Section 2.1) */
+} diffus_fan;
+
+/* Renderer options.
+ *  mode: DIFFUS_MODE_LITERAL uses R = |Z2-Z1|/(Z1+Z2) for both directions of
+ *    an interface, exactly as Eq. 1 prints it; DIFFUS_MODE_SIGNED uses
+ *    r = (Z2-Z1)/(Z1+Z2) forward and -r backward.  T = 2Z2/(Z1+Z2) and
+ *    T' = 2Z1/(Z1+Z2) in both.
+ *  Attenuation (Section 2.1, assumption 4): amplitude factor
+ *    a = 10^(-alpha f ds[cm] / 20) per sample cell and direction.
+ *  Speckle (Section 2.4), multiplicative on echo row k of ray j:
+ *    m = max(0, 1 + Ar z^pr n_r + Ag z^pg n_g),  z = (k+1)/S,
+ *    n_r = (sum of nu(k-Lr .. k+Lr)) / sqrt(2 Lr + 1), nu(k) white normals,
+ *    n_g = one normal per grain; the ray is cut into four depth bands
+ *    b = floor(4k/S) and grains in band b are 2^(gshift+b) rows long.
+ *    Normals are Irwin-Hall(4) sums of the bytes of a Philox4x32-10 word;
+ *    key = seed, counter = (group, ray, pose_ctr + pose, stream) with
+ *    stream 0 for nu (word k mod 4 of group floor(k/4)) and stream 1 for
+ *    grains (word cell mod 4 of group floor(cell/4), cell = b<<24 | index).
+ *  Blur (Section 2.4), after speckle: row k of ray j becomes the weighted
+ *    mean over rays j-W..j+W inside the fan with weights
+ *    exp(-m^2 / (2 s_k^2)), s_k = sigma0 + sigma1 (k+1)/S (in rays),
+ *    W = ceil(3 (sigma0 + sigma1)) <= 32.
+ *  refine: BF16 volumes only - one refinement pass of the per-ray depth
+ *    recurrence with the residual computed in FP64 (batched path). */
+typedef struct {
+    uint64_t seed;
+    int32_t mode;
+    int32_t speckle;            /* 0/1 */
+    double Ar, pr, Ag, pg;
+    int32_t Lr;                 /* 0..4 */
+    int32_t gshift;             /* 0..16 */
+    int32_t blur;               /* 0/1 */
+    int32_t refine;             /* 0/1 */
+    double sigma0, sigma1;      /* >= 0 */
+    uint32_t pose_ctr;          /* Philox pose word for pose 0 of the call */
+    uint32_t reserved;
+} diffus_params;
+
+/* ------------------------------------------------------------ single pose */
+
+/* Workspace bytes needed by diffus_render_fwd (with_bwd = 0) or by
+ * diffus_render_bwd (with_bwd = 1) for this volume, fan and parameters.
+ * Returns 0 for invalid arguments. */
+size_t diffus_workspace_bytes(const diffus_volume_desc *vd, const diffus_fan *fan,
+                              const diffus_params *prm, int32_t with_bwd);
+
+/* Forward render of one pose (Sections 2.3-2.4): writes image (device,
+ * float32 [n_rays][S]).  ray_valid (device int32[n_rays], nullable) receives
+ * the number of leading echo rows of each ray that are free of a pole of the
+ * depth system: the literal model of Eq. 1 can make det(A_k) vanish; row k
+ * needs det(A_k) and det(A_{k+1}) >= 1e-6, so ray_valid = k* - 1 for the
+ * first failing depth k*, or S.  Rows beyond ray_valid are written as
+ * computed.  vol is (device) float32 or bfloat16 per vd->dtype; pose is
+ * (device) float[6]; workspace (device) of diffus_workspace_bytes(..., 0)
+ * bytes, 256-byte aligned. */
+int diffus_render_fwd(const void *vol, const diffus_volume_desc *vd, const float *pose,
+                      const diffus_fan *fan, const diffus_params *prm, float *image,
+                      int32_t *ray_valid, uint32_t *status, void *workspace, size_t ws_bytes,
+                      diffus_stream_t stream);
+
+/* Backward of diffus_render_fwd for L = sum(grad_image * image): writes
+ * grad_vol (device float32, same dims as the volume, overwritten, nullable)
+ * and grad_pose (device float[6], overwritten, nullable).  The forward is
+ * recomputed per ray; nothing is kept from the forward call.  The volume
+ * gradient is gathered per brick without floating-point atomics, so both
+ * outputs are bitwise reproducible.  Workspace of
+ * diffus_workspace_bytes(..., 1) bytes. */
+int diffus_render_bwd(const void *vol, const diffus_volume_desc *vd, const float *pose,
+                      const diffus_fan *fan, const diffus_params *prm, const float *grad_image,
+                      float *grad_vol, float *grad_pose, uint32_t *status, void *workspace,
+                      size_t ws_bytes, diffus_stream_t stream);
+
+/* ---------------------------------------------------------------- batched */
+
+/* Launch schedule of the batched path.  rays_per_cta: warps (one ray each)
+ * per CTA of the persistent marches (2, 4 or 8); ctas_per_sm: resident CTAs
+ * per SM used to size the persistent grid; brick: poses per chunk of the
+ * volume-gradient gather (each chunk is one launch over the touched 8^3
+ * bricks).  Zero fields take defaults (4, 4, 16). */
+typedef struct {
+    int32_t rays_per_cta;
+    int32_t ctas_per_sm;
+    int32_t brick;
+    int32_t reserved;
+} diffus_schedule;
+
+/* Optional tracing of the batched call: when non-NULL, the library records
+ * each non-NULL event (a cudaEvent_t created by the caller) on the call's
+ * stream at the phase boundaries below, so a caller can time every phase of
+ * the step with cudaEventElapsedTime, also inside a captured graph. */
+enum {
+    DIFFUS_TR_START = 0,       /* before ray setup */
+    DIFFUS_TR_MARCH_FWD = 1,   /* after ray setup, before the forward march */
+    DIFFUS_TR_BLUR = 2,        /* after the forward march */
+    DIFFUS_TR_FWD_END = 3,     /* after the lateral blur */
+    DIFFUS_TR_MARCH_BWD = 4,   /* after the blur transpose */
+    DIFFUS_TR_POSE = 5,        /* after the adjoint march */
+    DIFFUS_TR_GATHER = 6,      /* after the pose reduction */
+    DIFFUS_TR_END = 7,         /* after the volume gather */
+    DIFFUS_TR_COUNT = 8
+};
+typedef struct {
+    void *event[DIFFUS_TR_COUNT];
+} diffus_trace;
+
+/* Size of the plan blob for P fans (host). */
+size_t diffus_batch_plan_bytes(const diffus_fan *fans, int32_t P);
+
+/* Host-only planning of a batch of P poses with their own fans: validates
+ * the fans, writes the image offsets (host int64[P+1]; pose p's image is
+ * images[img_offsets[p] .. img_offsets[p+1]) as [n_rays_p][S_p]), orders the
+ * rays longest first for the persistent queue and writes a self-contained
+ * plan into plan_host (host, diffus_batch_plan_bytes bytes).  The caller
+ * copies the plan to device memory once; diffus_render_batch reads it from
+ * there.  *ws_fwd / *ws_bwd receive the workspace bytes for forward-only
+ * and forward+backward calls. */
+int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan *fans, int32_t P,
+                      const diffus_params *prm, const diffus_schedule *sched, void *plan_host,
+                      size_t plan_bytes, int64_t *img_offsets, size_t *ws_fwd, size_t *ws_bwd);
+
+/* Forward (and, if grad_images is non-NULL, backward) render of all poses of
+ * a plan in persistent launches over a ray queue.  poses (device float
+ * [P][6]); plan_host (the host plan, read for sizes and launch shapes) and
+ * plan_dev (its device copy, 256-byte aligned, read by the kernels); images
+ * (device float32, img_offsets[P] values); grad_images (device, same
+ * layout, nullable); grad_vol (device float32 volume, overwritten,
+ * nullable); grad_poses (device float [P][6], overwritten, nullable);
+ * ray_valid (device int32, one per ray in pose order, nullable).  The plan
+ * must come from diffus_batch_plan with the same blur parameters
+ * (DIFFUS_E_PLAN otherwise).  Only kernels and async memsets are issued, so
+ * the call can be captured in a CUDA graph and replayed. */
+int diffus_render_batch(const void *vol, const diffus_volume_desc *vd, const float *poses,
+                        const void *plan_host, const void *plan_dev, const diffus_params *prm,
+                        float *images, int32_t *ray_valid, const float *grad_images, float *grad_vol,
+                        float *grad_poses, uint32_t *status, void *workspace, size_t ws_bytes,
+                        const diffus_trace *trace, diffus_stream_t stream);
+
+/* ------------------------------------------------------------------ misc */
+
+/* Philox4x32-10 (Salmon et al., SC'11), the generator behind the speckle of
+ * Section 2.4: out[i] = Philox(ctr[i], key) for n counters.  ctr and out are
+ * (device) uint32 [n][4], 16-byte aligned; key word 0 is the low half of
+ * `key`.  Exposed so that callers can reproduce or audit the speckle field. */
+int diffus_philox(const uint32_t *ctr, int64_t n, uint64_t key, uint32_t *out, diffus_stream_t stream);
+
+const char *diffus_strerror(int code);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int diffus_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIFFUS_H */

@@ -78,10 +78,11 @@ def _load():
             lib.or_blur.argtypes = [C.POINTER(_Params), dp, C.c_int, C.c_int, dp]
             lib.or_blur_T.argtypes = [C.POINTER(_Params), dp, C.c_int, C.c_int, dp]
             lib.or_render.argtypes = [C.c_void_p, C.POINTER(_Grid), dp, C.POINTER(_Fan), C.POINTER(_Params),
-                                      C.c_uint32, C.c_int, C.POINTER(C.c_int), dp, C.POINTER(C.c_int)]
+                                      C.c_uint32, C.c_int, C.POINTER(C.c_int), dp, C.POINTER(C.c_int), dp]
             lib.or_render_grad.argtypes = [C.c_void_p, C.POINTER(_Grid), dp, C.POINTER(_Fan), C.POINTER(_Params),
                                            C.c_uint32, dp, dp, dp]
             lib.or_num_threads.restype = C.c_int
+            lib.or_philox_many.argtypes = [C.POINTER(C.c_uint32), C.c_long, C.c_uint64, C.POINTER(C.c_uint32)]
             _lib = lib
     return _lib
 
@@ -198,6 +199,15 @@ def philox(ctr, key):
     return np.array(list(o), dtype=np.uint32)
 
 
+def philox_many(ctrs, key: int):
+    """Philox4x32-10 of an (n, 4) uint32 counter array under a 64-bit key."""
+    c = np.ascontiguousarray(np.asarray(ctrs, dtype=np.uint32))
+    out = np.zeros_like(c)
+    _load().or_philox_many(c.ctypes.data_as(C.POINTER(C.c_uint32)), c.shape[0], int(key) & (2**64 - 1),
+                           out.ctypes.data_as(C.POINTER(C.c_uint32)))
+    return out
+
+
 def speckle(params, pose_ctr: int, j: int, S: int):
     m = np.zeros(S)
     p = _params(params)
@@ -228,9 +238,11 @@ def blur_T(params, g):
     return out
 
 
-def render(vol, pose, fan, params, pose_ctr: int = 0, rays=None):
+def render(vol, pose, fan, params, pose_ctr: int = 0, rays=None, first_bad=False, dets=False):
     """Image rows (after speckle and blur) for the selected rays of one pose,
-    and their ill-posed flags."""
+    and their ill-posed flags (or, with first_bad=True, the first depth k
+    with det(A_k) < 1e-6 per ray, S+1 when none).  With dets=True a third
+    result holds det(A_k), k = 0..S, of every selected ray."""
     d = _vol32(vol)
     g = _grid(vol)
     f = _fan(fan)
@@ -242,12 +254,15 @@ def render(vol, pose, fan, params, pose_ctr: int = 0, rays=None):
     S = int(fan.n_samples)
     img = np.zeros((sel.size, S))
     ill = np.zeros(sel.size, dtype=np.int32)
+    det = np.zeros((sel.size, S + 1)) if dets else None
     rc = _load().or_render(d.ctypes.data, C.byref(g), _dp(pose), C.byref(f), C.byref(p), pose_ctr,
                            sel.size, sel.ctypes.data_as(C.POINTER(C.c_int)), _dp(img),
-                           ill.ctypes.data_as(C.POINTER(C.c_int)))
+                           ill.ctypes.data_as(C.POINTER(C.c_int)),
+                           _dp(det) if dets else C.POINTER(C.c_double)())
     if rc != 0:
         raise FloatingPointError("singular depth system in oracle render")
-    return img, ill.astype(bool)
+    flags = ill if first_bad else ill <= S
+    return (img, flags, det) if dets else (img, flags)
 
 
 def render_grad(vol, pose, fan, params, gimg, pose_ctr: int = 0, want_vol: bool = True):

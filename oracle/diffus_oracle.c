@@ -613,10 +613,11 @@ void or_blur_T(const or_params *p, const double *g, int n, int S, double *out)
 /* ------------------------------------------------------- full render */
 
 /* Echo rows of one ray before blur: y[k] = speckle[k] * (d0^(k+1) - d0^(k)).
- * ill receives 1 when the ray is ill-posed: some depth-k system has
- * det(A_k) < 1e-6 (a pole of the literal model or its neighbourhood). */
+ * first receives the first depth k (1..S) whose system has det(A_k) < 1e-6
+ * (a pole of the literal model or its neighbourhood), or S+1 if none; rows
+ * k <= first-2 use only well-posed depths. */
 static int ray_echo(const float *vol, const or_grid *g, const double pose[6], const or_fan *fan,
-                    const or_params *p, uint32_t pose_ctr, int j, double *y, int *ill)
+                    const or_params *p, uint32_t pose_ctr, int j, double *y, int *first, double *det_out)
 {
     int S = fan->n_samples;
     double *pos = malloc(sizeof(double) * 3 * (size_t)(S + 1));
@@ -628,18 +629,21 @@ static int ray_echo(const float *vol, const or_grid *g, const double pose[6], co
     for (int k = 0; k <= S; k++) Z[k] = or_trilinear(vol, g, pos + 3 * k, NULL);
     int rc = or_profile(Z, S, or_attenuation(fan), p->mode, 0, d0, det);
     or_speckle(p, pose_ctr, j, S, m);
-    int bad = 0;
-    for (int k = 1; k <= S; k++) if (!(det[k] >= 1e-6)) bad = 1;
+    int fb = S + 1;
+    for (int k = S; k >= 1; k--) if (!(det[k] >= 1e-6)) fb = k;
     for (int k = 0; k < S; k++) y[k] = m[k] * (d0[k + 1] - d0[k]);
-    *ill = bad;
+    *first = fb;
+    if (det_out) memcpy(det_out, det, sizeof(double) * (size_t)(S + 1));
     free(pos); free(Z); free(d0); free(det); free(m);
     return rc;
 }
 
 /* Render selected rays of one pose.  img receives n_sel rows of S values
- * (after speckle and blur); ill receives the per-row ill-posed flag. */
+ * (after speckle and blur); ill receives, per selected ray, the first
+ * ill-posed depth (S+1 when the ray has none). */
 int or_render(const float *vol, const or_grid *g, const double pose[6], const or_fan *fan,
-              const or_params *p, uint32_t pose_ctr, int n_sel, const int *sel, double *img, int *ill)
+              const or_params *p, uint32_t pose_ctr, int n_sel, const int *sel, double *img, int *ill,
+              double *det_sel)
 {
     int n = fan->n_rays, S = fan->n_samples, W = or_blur_halfwidth(p);
     char *need = calloc((size_t)n, 1);
@@ -650,13 +654,17 @@ int or_render(const float *vol, const or_grid *g, const double pose[6], const or
         }
     double *y = calloc((size_t)n * S, sizeof(double));
     int *illr = calloc((size_t)n, sizeof(int));
+    double *detr = det_sel ? calloc((size_t)n * (S + 1), sizeof(double)) : NULL;
     int rc = 0;
 #pragma omp parallel for schedule(dynamic, 1) reduction(| : rc)
     for (int j = 0; j < n; j++)
-        if (need[j]) rc |= ray_echo(vol, g, pose, fan, p, pose_ctr, j, y + (long)j * S, &illr[j]);
+        if (need[j])
+            rc |= ray_echo(vol, g, pose, fan, p, pose_ctr, j, y + (long)j * S, &illr[j],
+                           detr ? detr + (long)j * (S + 1) : NULL);
     for (int i = 0; i < n_sel; i++) {
         int j = sel[i];
         ill[i] = illr[j];
+        if (det_sel) memcpy(det_sel + (long)i * (S + 1), detr + (long)j * (S + 1), sizeof(double) * (size_t)(S + 1));
         for (int k = 0; k < S; k++) {
             if (!p->blur) { img[(long)i * S + k] = y[(long)j * S + k]; continue; }
             double num = 0.0, den = 0.0;
@@ -670,7 +678,7 @@ int or_render(const float *vol, const or_grid *g, const double pose[6], const or
             img[(long)i * S + k] = num / den;
         }
     }
-    free(need); free(y); free(illr);
+    free(need); free(y); free(illr); free(detr);
     return rc ? -1 : 0;
 }
 
@@ -746,4 +754,12 @@ int or_render_grad(const float *vol, const or_grid *g, const double pose[6], con
     }
     free(gy); free(gZall);
     return rc ? -1 : 0;
+}
+
+/* Philox4x32-10 of n counters (n x 4 words) under one 64-bit key. */
+void or_philox_many(const uint32_t *ctr, long n, uint64_t key, uint32_t *out)
+{
+    uint32_t k[2] = {(uint32_t)key, (uint32_t)(key >> 32)};
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < n; i++) or_philox4x32_10(ctr + 4 * i, k, out + 4 * i);
 }

@@ -1,0 +1,500 @@
+// Batched rendering of many poses with their own fans (uneven ray counts and
+// depths) in persistent launches over a device ray queue.
+//
+// diffus_batch_plan (host) lays out a self-contained plan: per-pose fan
+// table, per-ray (pose, ray) map and buffer offsets, the queue order (longest
+// rays first, so the persistent CTAs finish together) and the lateral-blur
+// tiles.  diffus_render_batch then launches only kernels and async memsets,
+// so a whole forward+backward step can be captured in one CUDA graph.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "gather.cuh"
+#include "host.hpp"
+#include "march_bwd.cuh"
+
+using namespace dfs;
+
+namespace dfs {
+MarchArgs make_march_args(const diffus_volume_desc *vd, const diffus_fan *fan, const diffus_params *prm);
+int launch_gather(const diffus_volume_desc *vd, const float *poses, const double *depth_dev, double depth_all,
+                  int P, int pose_chunk, const RayGeo *geo, const int *ray0, const float *gz, const long long *gz_off,
+                  PoseBox *boxes, int *list, int *count, float *grad_vol, cudaStream_t s);
+}  // namespace dfs
+
+namespace {
+
+constexpr uint32_t kPlanMagic = 0x44465350u;   // "DFSP"
+
+struct PlanPose {
+    int32_t n_rays, S;
+    double fov, depth;
+    float a2;
+    int32_t W;
+    int64_t img_off;
+};
+
+struct BlurTile {
+    int32_t pose, j0, k0, pad;
+};
+
+struct PlanHeader {
+    uint32_t magic;
+    int32_t P;
+    int64_t total_rays, total_img, total_gz, total_ckpt, n_tiles;
+    int32_t max_S, blurW;
+    int32_t warps, ctas_per_sm, pose_chunk, brick;
+    int64_t off_pose, off_depth, off_ray0, off_ray_pose, off_ray_j, off_order, off_row_off, off_gz_off, off_ck_off,
+        off_tiles;
+    int64_t bytes;
+    uint64_t params_fp;   // fingerprint of the parameters the plan was made for
+};
+
+template <typename T>
+const T *at(const void *base, int64_t off) { return (const T *)((const char *)base + off); }
+template <typename T>
+T *at_mut(void *base, int64_t off) { return (T *)((char *)base + off); }
+
+uint64_t params_fingerprint(const diffus_params *p)
+{
+    // fields that change the plan (blur width)
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void *d, size_t n) {
+        const unsigned char *c = (const unsigned char *)d;
+        for (size_t i = 0; i < n; i++) h = (h ^ c[i]) * 1099511628211ull;
+    };
+    mix(&p->blur, sizeof p->blur);
+    mix(&p->sigma0, sizeof p->sigma0);
+    mix(&p->sigma1, sizeof p->sigma1);
+    return h;
+}
+
+struct PlanSizes {
+    int64_t off[11];
+    int64_t bytes;
+};
+
+PlanSizes plan_sizes(int P, int64_t total_rays, int64_t n_tiles)
+{
+    PlanSizes z;
+    int64_t o = (int64_t)align256(sizeof(PlanHeader));
+    auto put = [&](int i, int64_t n) {
+        z.off[i] = o;
+        o += (int64_t)align256((size_t)n);
+    };
+    put(0, sizeof(PlanPose) * (int64_t)P);
+    put(1, sizeof(double) * (int64_t)P);
+    put(2, sizeof(int32_t) * (int64_t)(P + 1));
+    put(3, sizeof(int32_t) * total_rays);
+    put(4, sizeof(int32_t) * total_rays);
+    put(5, sizeof(int32_t) * total_rays);
+    put(6, sizeof(int64_t) * total_rays);
+    put(7, sizeof(int64_t) * total_rays);
+    put(8, sizeof(int64_t) * total_rays);
+    put(9, sizeof(BlurTile) * n_tiles);
+    z.bytes = o;
+    return z;
+}
+
+int64_t count_tiles(const diffus_fan *fans, int P)
+{
+    int64_t t = 0;
+    for (int p = 0; p < P; p++)
+        t += (int64_t)((fans[p].n_samples + kBlurRows - 1) / kBlurRows) * ((fans[p].n_rays + kBlurRays - 1) / kBlurRays);
+    return t;
+}
+
+struct BatchLayout {
+    RayGeo *geo;
+    float *y;        // pre-blur rows (blur on)
+    unsigned *counter;
+    float *gy;       // blur transpose of grad_images (blur on)
+    float *gz;
+    double *part;
+    float4 *ckpt;
+    PoseBox *boxes;
+    int *list, *count;
+    size_t fwd_bytes, bytes;
+};
+
+BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc *vd, bool blur)
+{
+    Carve c(ws);
+    BatchLayout L;
+    L.geo = c.take<RayGeo>((size_t)H.total_rays);
+    L.counter = c.take<unsigned>(4);
+    L.y = blur ? c.take<float>((size_t)H.total_img) : nullptr;
+    L.fwd_bytes = c.used;
+    size_t nb = (size_t)((vd->nx + kBrick - 1) / kBrick) * ((vd->ny + kBrick - 1) / kBrick) *
+                ((vd->nz + kBrick - 1) / kBrick);
+    L.gy = blur ? c.take<float>((size_t)H.total_img) : nullptr;
+    L.gz = c.take<float>((size_t)H.total_gz);
+    L.part = c.take<double>(6 * (size_t)H.total_rays);
+    L.ckpt = c.take<float4>((size_t)H.total_ckpt);
+    L.boxes = c.take<PoseBox>((size_t)H.P);
+    L.list = c.take<int>(nb);
+    L.count = c.take<int>(1);
+    L.bytes = c.used;
+    return L;
+}
+
+// ------------------------------------------------------------------ kernels
+
+struct BatchDev {
+    const PlanPose *pose;
+    const int32_t *ray_pose, *ray_j, *order;
+    const int64_t *row_off, *gz_off, *ck_off;
+    int64_t total_rays;
+};
+
+__global__ void k_batch_setup(const float *__restrict__ poses, BatchDev B, VolPlace vp, RayGeo *__restrict__ geo)
+{
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= B.total_rays) return;
+    const int p = B.ray_pose[r];
+    const PlanPose pp = B.pose[p];
+    FanDev fd{pp.n_rays, pp.S, pp.fov, pp.depth};
+    RayGeo rg;
+    setup_ray(poses + 6 * (size_t)p, p, B.ray_j[r], fd, vp, rg);
+    geo[r] = rg;
+}
+
+// Persistent forward: each warp takes rays from the queue (longest first).
+template <typename T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_batch_fwd(const T *__restrict__ vol, MarchArgs A, BatchDev B,
+                                                          const RayGeo *__restrict__ geo, float *__restrict__ out,
+                                                          int *__restrict__ valid, uint32_t *__restrict__ status,
+                                                          unsigned *__restrict__ counter)
+{
+    __shared__ float buf[WARPS][kSegPad];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned q = 0;
+        if (lane == 0) q = atomicAdd(counter, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if ((int64_t)q >= B.total_rays) break;
+        const int r = B.order[q];
+        RayGeo rg = geo[r];
+        MarchArgs Ap = A;
+        Ap.a2 = B.pose[rg.pose].a2;
+        RayOut o{out + B.row_off[r], valid ? valid + r : nullptr, status};
+        march_fwd_ray<T>(vol, Ap, rg, o, buf[w]);
+        __syncwarp();
+    }
+}
+
+template <typename T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_batch_bwd(const T *__restrict__ vol, MarchArgs A, BatchDev B,
+                                                          const RayGeo *__restrict__ geo,
+                                                          const float *__restrict__ gy, float *__restrict__ gz,
+                                                          double *__restrict__ part, float4 *__restrict__ ckpt,
+                                                          unsigned *__restrict__ counter)
+{
+    __shared__ BwdSmem sm[WARPS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned q = 0;
+        if (lane == 0) q = atomicAdd(counter, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if ((int64_t)q >= B.total_rays) break;
+        const int r = B.order[q];
+        RayGeo rg = geo[r];
+        MarchArgs Ap = A;
+        Ap.a2 = B.pose[rg.pose].a2;
+        march_bwd_ray<T>(vol, Ap, rg, gy + B.row_off[r], gz + B.gz_off[r], part + 6 * (size_t)r,
+                         ckpt + B.ck_off[r], sm[w]);
+        __syncwarp();
+    }
+}
+
+template <bool TRANSPOSE>
+__global__ void __launch_bounds__(kBlurThreads) k_batch_blur(const float *__restrict__ in, float *__restrict__ out,
+                                                             const PlanPose *__restrict__ poses,
+                                                             const BlurTile *__restrict__ tiles, int64_t n_tiles,
+                                                             BlurArgs b)
+{
+    extern __shared__ float dyn[];
+    float *wsm = dyn;
+    float *sm = dyn + (kMaxW + 1) * 32;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const BlurTile tl = tiles[t];
+        const PlanPose pp = poses[tl.pose];
+        blur_tile<TRANSPOSE>(in + pp.img_off, out + pp.img_off, pp.n_rays, pp.S, b, tl.j0, tl.k0, sm, wsm);
+        __syncthreads();
+    }
+}
+
+int sm_count()
+{
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+template <typename T, int WARPS>
+void launch_fwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out, int *valid,
+                  uint32_t *status, unsigned *counter, int grid, cudaStream_t s)
+{
+    k_batch_fwd<T, WARPS><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status, counter);
+}
+
+template <typename T, int WARPS>
+void launch_bwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, const float *gy,
+                  float *gz, double *part, float4 *ckpt, unsigned *counter, int grid, cudaStream_t s)
+{
+    k_batch_bwd<T, WARPS><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, gy, gz, part, ckpt, counter);
+}
+
+template <typename T>
+int launch_fwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out,
+                 int *valid, uint32_t *status, unsigned *counter, int grid, cudaStream_t s)
+{
+    switch (warps) {
+    case 2: launch_fwd_t<T, 2>(vol, A, B, geo, out, valid, status, counter, grid, s); break;
+    case 4: launch_fwd_t<T, 4>(vol, A, B, geo, out, valid, status, counter, grid, s); break;
+    case 8: launch_fwd_t<T, 8>(vol, A, B, geo, out, valid, status, counter, grid, s); break;
+    default: return DIFFUS_E_PLAN;
+    }
+    return DIFFUS_OK;
+}
+
+template <typename T>
+int launch_bwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, const float *gy,
+                 float *gz, double *part, float4 *ckpt, unsigned *counter, int grid, cudaStream_t s)
+{
+    switch (warps) {
+    case 2: launch_bwd_t<T, 2>(vol, A, B, geo, gy, gz, part, ckpt, counter, grid, s); break;
+    case 4: launch_bwd_t<T, 4>(vol, A, B, geo, gy, gz, part, ckpt, counter, grid, s); break;
+    case 8: launch_bwd_t<T, 8>(vol, A, B, geo, gy, gz, part, ckpt, counter, grid, s); break;
+    default: return DIFFUS_E_PLAN;
+    }
+    return DIFFUS_OK;
+}
+
+}  // namespace
+
+namespace dfs {
+__global__ void k_pose_reduce_batch(const double *__restrict__ part, const int *__restrict__ ray0, int P,
+                                    float *__restrict__ grad_pose)
+{
+    const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (p >= P) return;
+    const int a = ray0[p], b = ray0[p + 1];
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = a + lane; j < b; j += 32)
+        for (int q = 0; q < 6; q++) s[q] += part[6 * (size_t)j + q];
+    for (int q = 0; q < 6; q++) {
+        double v = s[q];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) grad_pose[6 * p + q] = (float)v;
+    }
+}
+}  // namespace dfs
+
+// ---------------------------------------------------------------- entry points
+
+extern "C" size_t diffus_batch_plan_bytes(const diffus_fan *fans, int32_t P)
+{
+    if (!fans || P < 1) return 0;
+    int64_t total_rays = 0;
+    for (int p = 0; p < P; p++) {
+        if (fans[p].n_rays < 1 || fans[p].n_samples < 1) return 0;
+        total_rays += fans[p].n_rays;
+    }
+    if (total_rays > INT32_MAX) return 0;
+    return (size_t)plan_sizes(P, total_rays, count_tiles(fans, P)).bytes;
+}
+
+extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan *fans, int32_t P,
+                                 const diffus_params *prm, const diffus_schedule *sched, void *plan_host,
+                                 size_t plan_bytes, int64_t *img_offsets, size_t *ws_fwd, size_t *ws_bwd)
+{
+    int rc;
+    if ((rc = check_vol(vd))) return rc;
+    if ((rc = check_params(prm))) return rc;
+    if (!fans || !plan_host || !img_offsets) return DIFFUS_E_NULL;
+    if (P < 1) return DIFFUS_E_DIMS;
+    int64_t total_rays = 0, total_img = 0, total_gz = 0, total_ck = 0;
+    int max_S = 0;
+    for (int p = 0; p < P; p++) {
+        if ((rc = check_fan(&fans[p], vd))) return rc;
+        total_rays += fans[p].n_rays;
+        total_img += (int64_t)fans[p].n_rays * fans[p].n_samples;
+        total_gz += (int64_t)fans[p].n_rays * (fans[p].n_samples + 1);
+        total_ck += (int64_t)fans[p].n_rays * ((fans[p].n_samples + kSeg - 1) / kSeg);
+        max_S = std::max(max_S, (int)fans[p].n_samples);
+    }
+    if (total_rays > INT32_MAX) return DIFFUS_E_DIMS;
+    const int64_t n_tiles = count_tiles(fans, P);
+    PlanSizes z = plan_sizes(P, total_rays, n_tiles);
+    if (plan_bytes < (size_t)z.bytes) return DIFFUS_E_WORKSPACE;
+
+    diffus_schedule sc = sched ? *sched : diffus_schedule{0, 0, 0, 0};
+    if (sc.rays_per_cta == 0) sc.rays_per_cta = 4;
+    if (sc.ctas_per_sm == 0) sc.ctas_per_sm = 4;
+    if (sc.brick == 0) sc.brick = 16;   // poses per gather chunk
+    if (sc.rays_per_cta != 2 && sc.rays_per_cta != 4 && sc.rays_per_cta != 8) return DIFFUS_E_PARAM;
+    if (sc.ctas_per_sm < 1 || sc.ctas_per_sm > 32 || sc.brick < 1) return DIFFUS_E_PARAM;
+
+    memset(plan_host, 0, (size_t)z.bytes);
+    PlanHeader &H = *(PlanHeader *)plan_host;
+    H.magic = kPlanMagic;
+    H.P = P;
+    H.total_rays = total_rays;
+    H.total_img = total_img;
+    H.total_gz = total_gz;
+    H.total_ckpt = total_ck;
+    H.n_tiles = n_tiles;
+    H.max_S = max_S;
+    H.blurW = blur_halfwidth(prm);
+    H.warps = sc.rays_per_cta;
+    H.ctas_per_sm = sc.ctas_per_sm;
+    H.pose_chunk = sc.brick;
+    H.brick = kBrick;
+    H.off_pose = z.off[0]; H.off_depth = z.off[1]; H.off_ray0 = z.off[2]; H.off_ray_pose = z.off[3];
+    H.off_ray_j = z.off[4]; H.off_order = z.off[5]; H.off_row_off = z.off[6]; H.off_gz_off = z.off[7];
+    H.off_ck_off = z.off[8]; H.off_tiles = z.off[9];
+    H.bytes = z.bytes;
+    H.params_fp = params_fingerprint(prm);
+
+    PlanPose *pp = at_mut<PlanPose>(plan_host, H.off_pose);
+    double *depth = at_mut<double>(plan_host, H.off_depth);
+    int32_t *ray0 = at_mut<int32_t>(plan_host, H.off_ray0);
+    int32_t *ray_pose = at_mut<int32_t>(plan_host, H.off_ray_pose);
+    int32_t *ray_j = at_mut<int32_t>(plan_host, H.off_ray_j);
+    int32_t *order = at_mut<int32_t>(plan_host, H.off_order);
+    int64_t *row_off = at_mut<int64_t>(plan_host, H.off_row_off);
+    int64_t *gz_off = at_mut<int64_t>(plan_host, H.off_gz_off);
+    int64_t *ck_off = at_mut<int64_t>(plan_host, H.off_ck_off);
+    BlurTile *tiles = at_mut<BlurTile>(plan_host, H.off_tiles);
+
+    int64_t r = 0, img = 0, g = 0, ck = 0, t = 0;
+    for (int p = 0; p < P; p++) {
+        const diffus_fan &f = fans[p];
+        double a = attenuation_a(&f);
+        pp[p] = PlanPose{f.n_rays, f.n_samples, f.fov_rad, f.depth_mm, (float)(a * a), H.blurW, img};
+        depth[p] = f.depth_mm;
+        ray0[p] = (int32_t)r;
+        img_offsets[p] = img;
+        const int nseg = (f.n_samples + kSeg - 1) / kSeg;
+        for (int j = 0; j < f.n_rays; j++, r++) {
+            ray_pose[r] = p;
+            ray_j[r] = j;
+            row_off[r] = img + (int64_t)j * f.n_samples;
+            gz_off[r] = g;
+            ck_off[r] = ck;
+            g += f.n_samples + 1;
+            ck += nseg;
+        }
+        for (int k0 = 0; k0 < f.n_samples; k0 += kBlurRows)
+            for (int j0 = 0; j0 < f.n_rays; j0 += kBlurRays) tiles[t++] = BlurTile{p, j0, k0, 0};
+        img += (int64_t)f.n_rays * f.n_samples;
+    }
+    ray0[P] = (int32_t)r;
+    img_offsets[P] = img;
+    // longest rays first; ties in ray order (stable)
+    std::vector<int32_t> ord((size_t)total_rays);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(),
+                     [&](int32_t x, int32_t y) { return pp[ray_pose[x]].S > pp[ray_pose[y]].S; });
+    std::copy(ord.begin(), ord.end(), order);
+
+    BatchLayout L = batch_layout(nullptr, H, vd, prm->blur != 0);
+    if (ws_fwd) *ws_fwd = L.fwd_bytes;
+    if (ws_bwd) *ws_bwd = L.bytes;
+    return DIFFUS_OK;
+}
+
+extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd, const float *poses,
+                                   const void *plan_host, const void *plan_dev, const diffus_params *prm,
+                                   float *images, int32_t *ray_valid, const float *grad_images, float *grad_vol,
+                                   float *grad_poses, uint32_t *status, void *workspace, size_t ws_bytes,
+                                   const diffus_trace *trace, diffus_stream_t stream)
+{
+    int rc;
+    if ((rc = check_vol(vd))) return rc;
+    if ((rc = check_params(prm))) return rc;
+    if (!vol || !poses || !plan_host || !plan_dev || !images || !workspace) return DIFFUS_E_NULL;
+    const PlanHeader &H = *(const PlanHeader *)plan_host;
+    if (H.magic != kPlanMagic || H.params_fp != params_fingerprint(prm) || H.blurW != blur_halfwidth(prm))
+        return DIFFUS_E_PLAN;
+    size_t el = vd->dtype == DIFFUS_F32 ? 4 : 2;
+    if (((uintptr_t)vol) % el || ((uintptr_t)poses) % 4 || ((uintptr_t)images) % 4 ||
+        ((uintptr_t)workspace) % 256 || ((uintptr_t)plan_dev) % 256)
+        return DIFFUS_E_ALIGN;
+    const bool bwd = grad_images != nullptr;
+    BatchLayout L = batch_layout(workspace, H, vd, prm->blur != 0);
+    if (ws_bytes < (bwd ? L.bytes : L.fwd_bytes)) return DIFFUS_E_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto mark = [&](int i) {
+        if (trace && trace->event[i]) cudaEventRecord((cudaEvent_t)trace->event[i], s);
+    };
+
+    BatchDev B;
+    B.pose = at<PlanPose>(plan_dev, H.off_pose);
+    B.ray_pose = at<int32_t>(plan_dev, H.off_ray_pose);
+    B.ray_j = at<int32_t>(plan_dev, H.off_ray_j);
+    B.order = at<int32_t>(plan_dev, H.off_order);
+    B.row_off = at<int64_t>(plan_dev, H.off_row_off);
+    B.gz_off = at<int64_t>(plan_dev, H.off_gz_off);
+    B.ck_off = at<int64_t>(plan_dev, H.off_ck_off);
+    B.total_rays = H.total_rays;
+
+    if (status && cudaMemsetAsync(status, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
+    if (cudaMemsetAsync(L.counter, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
+    mark(DIFFUS_TR_START);
+    k_batch_setup<<<(unsigned)((H.total_rays + 127) / 128), 128, 0, s>>>(poses, B, make_place(vd), L.geo);
+    mark(DIFFUS_TR_MARCH_FWD);
+
+    // march parameters shared by all poses (a^2 comes from the pose table)
+    diffus_fan dummy{1, 1, 0.0, 1.0, 0.0, 0.0};
+    MarchArgs A = make_march_args(vd, &dummy, prm);
+    const int grid = sm_count() * H.ctas_per_sm;
+    float *march_out = prm->blur ? L.y : images;
+    if (vd->dtype == DIFFUS_F32)
+        rc = launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0, grid, s);
+    else
+        rc = launch_fwd_w<unsigned short>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0,
+                                          grid, s);
+    if (rc) return rc;
+    mark(DIFFUS_TR_BLUR);
+    BlurArgs bl{(float)prm->sigma0, (float)prm->sigma1, H.blurW};
+    const int tgrid = (int)std::min<int64_t>(H.n_tiles, (int64_t)sm_count() * 8);
+    const PlanPose *dpose = at<PlanPose>(plan_dev, H.off_pose);
+    const BlurTile *dtiles = at<BlurTile>(plan_dev, H.off_tiles);
+    if (prm->blur)
+        k_batch_blur<false><<<tgrid, kBlurThreads, blur_smem_bytes(H.blurW), s>>>(L.y, images, dpose, dtiles,
+                                                                                 H.n_tiles, bl);
+    mark(DIFFUS_TR_FWD_END);
+    if ((rc = launch_status())) return rc;
+    if (!bwd) return DIFFUS_OK;
+
+    if (((uintptr_t)grad_images) % 4 || (grad_vol && ((uintptr_t)grad_vol) % 4) ||
+        (grad_poses && ((uintptr_t)grad_poses) % 4))
+        return DIFFUS_E_ALIGN;
+    const float *gy = grad_images;
+    if (prm->blur) {
+        k_batch_blur<true><<<tgrid, kBlurThreads, blur_smem_bytes(H.blurW), s>>>(grad_images, L.gy, dpose, dtiles,
+                                                                                H.n_tiles, bl);
+        gy = L.gy;
+    }
+    mark(DIFFUS_TR_MARCH_BWD);
+    if (vd->dtype == DIFFUS_F32)
+        rc = launch_bwd_w<float>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, grid, s);
+    else
+        rc = launch_bwd_w<unsigned short>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, grid,
+                                          s);
+    if (rc) return rc;
+    mark(DIFFUS_TR_POSE);
+    const int32_t *ray0 = at<int32_t>(plan_dev, H.off_ray0);
+    if (grad_poses) k_pose_reduce_batch<<<(H.P + 3) / 4, 128, 0, s>>>(L.part, ray0, H.P, grad_poses);
+    mark(DIFFUS_TR_GATHER);
+    if (grad_vol)
+        rc = launch_gather(vd, poses, at<double>(plan_dev, H.off_depth), 0.0, H.P, H.pose_chunk, L.geo, ray0, L.gz,
+                           (const long long *)B.gz_off, L.boxes, L.list, L.count, grad_vol, s);
+    mark(DIFFUS_TR_END);
+    return rc ? rc : launch_status();
+}

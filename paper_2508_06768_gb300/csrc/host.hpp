@@ -1,0 +1,124 @@
+// Host-side validation and workspace layout shared by the entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "diffus.h"
+#include "kernels_fwd.cuh"
+
+namespace dfs {
+
+inline bool finite_d(double x) { return std::isfinite(x); }
+
+inline int check_vol(const diffus_volume_desc *vd)
+{
+    if (!vd) return DIFFUS_E_NULL;
+    if (vd->dtype != DIFFUS_F32 && vd->dtype != DIFFUS_BF16) return DIFFUS_E_DTYPE;
+    if (vd->nx < 2 || vd->ny < 2 || vd->nz < 2) return DIFFUS_E_DIMS;
+    // 32-bit voxel offsets
+    if ((double)vd->nx * vd->ny * vd->nz >= 2147483647.0) return DIFFUS_E_DIMS;
+    if (!(vd->sx > 0 && vd->sy > 0 && vd->sz > 0)) return DIFFUS_E_PARAM;
+    if (!finite_d(vd->sx) || !finite_d(vd->sy) || !finite_d(vd->sz)) return DIFFUS_E_PARAM;
+    if (!finite_d(vd->ox) || !finite_d(vd->oy) || !finite_d(vd->oz)) return DIFFUS_E_PARAM;
+    return DIFFUS_OK;
+}
+
+inline int check_fan(const diffus_fan *f, const diffus_volume_desc *vd)
+{
+    if (!f) return DIFFUS_E_NULL;
+    if (f->n_rays < 1 || f->n_rays > (1 << 20)) return DIFFUS_E_DIMS;
+    if (f->n_samples < 1 || f->n_samples > (1 << 22)) return DIFFUS_E_DIMS;
+    if (!(f->fov_rad >= 0.0 && f->fov_rad < 3.14159265358979)) return DIFFUS_E_PARAM;
+    if (!(f->depth_mm > 0.0) || !finite_d(f->depth_mm)) return DIFFUS_E_PARAM;
+    if (!(f->f_mhz >= 0.0) || !finite_d(f->f_mhz)) return DIFFUS_E_PARAM;
+    if (!(f->alpha_db_cm_mhz >= 0.0) || !finite_d(f->alpha_db_cm_mhz)) return DIFFUS_E_PARAM;
+    // fixed-point positions: the ray must stay within 2^29 voxels
+    double smin = fmin(vd->sx, fmin(vd->sy, vd->sz));
+    if (f->depth_mm / smin > 536870912.0) return DIFFUS_E_PARAM;
+    return DIFFUS_OK;
+}
+
+inline int check_params(const diffus_params *p)
+{
+    if (!p) return DIFFUS_E_NULL;
+    if (p->mode != DIFFUS_MODE_LITERAL && p->mode != DIFFUS_MODE_SIGNED) return DIFFUS_E_PARAM;
+    if (p->speckle != 0 && p->speckle != 1) return DIFFUS_E_PARAM;
+    if (p->blur != 0 && p->blur != 1) return DIFFUS_E_PARAM;
+    if (p->refine != 0 && p->refine != 1) return DIFFUS_E_PARAM;
+    if (p->Lr < 0 || p->Lr > 4) return DIFFUS_E_PARAM;
+    if (p->gshift < 0 || p->gshift > 16) return DIFFUS_E_PARAM;
+    double v[6] = {p->Ar, p->pr, p->Ag, p->pg, p->sigma0, p->sigma1};
+    for (double x : v)
+        if (!finite_d(x)) return DIFFUS_E_PARAM;
+    if (p->sigma0 < 0 || p->sigma1 < 0) return DIFFUS_E_PARAM;
+    if (p->blur && ceil(3.0 * (p->sigma0 + p->sigma1)) > kMaxW) return DIFFUS_E_PARAM;
+    return DIFFUS_OK;
+}
+
+inline int blur_halfwidth(const diffus_params *p)
+{
+    if (!p->blur) return 0;
+    double s = p->sigma0 + p->sigma1;
+    return s > 0.0 ? (int)ceil(3.0 * s) : 0;
+}
+
+inline double attenuation_a(const diffus_fan *f)
+{
+    double ds_cm = f->depth_mm / (double)f->n_samples / 10.0;
+    return pow(10.0, -f->alpha_db_cm_mhz * f->f_mhz * ds_cm / 20.0);
+}
+
+inline Speckle make_speckle(const diffus_params *p)
+{
+    Speckle s;
+    s.Ar = (float)p->Ar;
+    s.pr = (float)p->pr;
+    s.Ag = (float)p->Ag;
+    s.pg = (float)p->pg;
+    float sc = (float)(1.0 / sqrt(2.0 * p->Lr + 1.0));
+    for (int d = -4; d <= 4; d++) s.wr[d + 4] = (d >= -p->Lr && d <= p->Lr) ? sc : 0.0f;
+    s.gshift = p->gshift;
+    s.on = p->speckle;
+    s.key0 = (uint32_t)(p->seed & 0xffffffffu);
+    s.key1 = (uint32_t)(p->seed >> 32);
+    s.pose_ctr = p->pose_ctr;
+    return s;
+}
+
+inline VolGeo make_volgeo(const diffus_volume_desc *vd)
+{
+    return {vd->nx, vd->ny, vd->nz, (float)(1.0 / vd->sx), (float)(1.0 / vd->sy), (float)(1.0 / vd->sz)};
+}
+
+inline VolPlace make_place(const diffus_volume_desc *vd)
+{
+    return {vd->sx, vd->sy, vd->sz, vd->ox, vd->oy, vd->oz};
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Bump allocator over the caller's workspace.
+struct Carve {
+    char *base;
+    size_t used = 0;
+    explicit Carve(void *p) : base((char *)p) {}
+    template <typename T>
+    T *take(size_t count)
+    {
+        T *p = base ? (T *)(base + used) : nullptr;
+        used += align256(count * sizeof(T));
+        return p;
+    }
+};
+
+inline int launch_status()
+{
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DIFFUS_OK : DIFFUS_E_LAUNCH;
+}
+
+}  // namespace dfs

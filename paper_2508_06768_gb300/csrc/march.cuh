@@ -1,0 +1,269 @@
+// Warp-per-ray march: samples the impedance along a ray, forms the interface
+// coefficients (Eq. 1), solves every truncated depth system of Eq. 4 at once
+// with a 2x2 prefix scan, and extracts the echo rows (Section 2.4).
+//
+// Why a scan solves Eq. 4: eliminating the coupled recurrences of Eq. 2 from
+// the deepest interface upward gives rho_i = d_i / g_i as a Moebius map of
+// rho_{i+1}; the composition of the maps of interfaces 0..k-1 is the matrix
+// product P_k = M_0 ... M_{k-1}, and d_0^(k) = P_k[0][1] / P_k[1][1].  The
+// echo row k, d_0^(k+1) - d_0^(k), then has the cancellation-free form
+//     e_k = x_k det(P_k) / (P_k[1][1] (P_k[1][0] x_k + P_k[1][1]))
+// with x_k = M_k[0][1], det(P_k) = prod_{i<k} a^2 (1 - r_i^2), which needs
+// only the bottom row b_k = (P_k[1][0], P_k[1][1]).  P_k[1][1] equals
+// det(A_k), the determinant of the depth-k system, and flags poles.
+//
+// A ray's S interfaces are processed in segments of 256: 32 lanes own 8
+// consecutive interfaces each; the lanes' chunk products are combined by a
+// warp scan (5 shuffle levels) and carried from segment to segment.
+#pragma once
+
+#include "common.cuh"
+
+namespace dfs {
+
+struct MarchArgs {
+    VolGeo g;
+    float a2;         // a^2, round-trip amplitude factor of one cell
+    int mode;
+    Speckle sp;
+};
+
+struct RayOut {
+    float *row;       // output row [S] (image or pre-blur buffer)
+    int *valid;       // nullable: leading pole-free rows
+    uint32_t *status; // nullable
+};
+
+__device__ __forceinline__ int smem_idx(int x) { return x + (x >> 3); }
+
+__device__ __forceinline__ void sample_pos(const RayGeo &rg, int k, long long &X, long long &Y, long long &Z)
+{
+    X = rg.X0[0] + (long long)k * rg.DX[0];
+    Y = rg.X0[1] + (long long)k * rg.DX[1];
+    Z = rg.X0[2] + (long long)k * rg.DX[2];
+}
+
+// Phase A of a segment: samples base+1 .. base+256 lane-interleaved and
+// writes r_i (i = base..base+255, 0 past the ray) into buf[smem_idx(i-base)].
+// (czr, cdz) carries the sample at `base` in and the one at base+256 out.
+template <typename T>
+__device__ __forceinline__ void seg_reflections(const T *__restrict__ vol, const VolGeo &g, const RayGeo &rg,
+                                                int base, float &czr, float &cdz, float *__restrict__ buf)
+{
+    const int lane = threadIdx.x & 31;
+    const int S = rg.S;
+    float pzr = czr, pdz = cdz;
+#pragma unroll
+    for (int t = 0; t < kChunk; t++) {
+        int k = base + t * kWarp + lane + 1;
+        float zr = 0.0f, dz = 0.0f;
+        if (k <= S) {
+            long long X, Y, Z;
+            sample_pos(rg, k, X, Y, Z);
+            sample_z<T, false>(vol, g, X, Y, Z, zr, dz);
+        }
+        float lzr = __shfl_up_sync(0xffffffffu, zr, 1);
+        float ldz = __shfl_up_sync(0xffffffffu, dz, 1);
+        if (lane == 0) { lzr = pzr; ldz = pdz; }
+        float r = (k - 1 < S) ? refl(lzr, ldz, zr, dz) : 0.0f;
+        buf[smem_idx(t * kWarp + lane)] = r;
+        pzr = __shfl_sync(0xffffffffu, zr, 31);
+        pdz = __shfl_sync(0xffffffffu, dz, 31);
+    }
+    czr = pzr;
+    cdz = pdz;
+}
+
+// Chunk product Q = M_{i0} ... M_{i0+7} (identity past the ray) and its
+// determinant dq.
+__device__ __forceinline__ void chunk_product(const float *rr, int i0, int S, float a2, int mode, Mat2 &Q, float &dq)
+{
+    Q = mat_ident();
+    dq = 1.0f;
+#pragma unroll
+    for (int t = 0; t < kChunk; t++) {
+        if (i0 + t < S) {
+            Xfer x = xfer(rr[t], a2, mode);
+            mat_mul_xfer(Q, x);
+            dq *= x.delta;
+        }
+    }
+}
+
+// Warp scan of chunk products: returns the exclusive prefix (E, de) of this
+// lane and the segment total (Qall, dall).
+__device__ __forceinline__ void warp_scan_prefix(Mat2 Q, float dq, Mat2 &E, float &de, Mat2 &Qall, float &dall)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < kWarp; off <<= 1) {
+        Mat2 P = shfl_up_mat(Q, off);
+        float pd = __shfl_up_sync(0xffffffffu, dq, off);
+        if (lane >= off) {
+            Q = mat_mul(P, Q);
+            dq = pd * dq;
+        }
+    }
+    E = shfl_up_mat(Q, 1);
+    de = __shfl_up_sync(0xffffffffu, dq, 1);
+    if (lane == 0) {
+        E = mat_ident();
+        de = 1.0f;
+    }
+    Qall = shfl_mat(Q, 31);
+    dall = __shfl_sync(0xffffffffu, dq, 31);
+}
+
+// Radial white normals of group q (4 rows 4q..4q+3), stream 0.
+__device__ __forceinline__ uint4 radial_group(const Speckle &sp, int q, int ray, uint32_t pose)
+{
+    return philox10(make_uint4((uint32_t)q, (uint32_t)ray, pose, 0u), sp.key0, sp.key1);
+}
+
+__device__ __forceinline__ uint4 shfl_up_u4(uint4 v, int off)
+{
+    return make_uint4(__shfl_up_sync(0xffffffffu, v.x, off), __shfl_up_sync(0xffffffffu, v.y, off),
+                      __shfl_up_sync(0xffffffffu, v.z, off), __shfl_up_sync(0xffffffffu, v.w, off));
+}
+
+__device__ __forceinline__ uint4 shfl_down_u4(uint4 v, int off)
+{
+    return make_uint4(__shfl_down_sync(0xffffffffu, v.x, off), __shfl_down_sync(0xffffffffu, v.y, off),
+                      __shfl_down_sync(0xffffffffu, v.z, off), __shfl_down_sync(0xffffffffu, v.w, off));
+}
+
+// Speckle factors of this lane's chunk rows i0 .. i0+7 (Section 2.4).  All
+// 32 lanes must call it together (the radial window is shared by shuffles).
+__device__ __forceinline__ void chunk_speckle(const Speckle &sp, int i0, int S, int ray, uint32_t pose,
+                                              float *m)
+{
+    const int lane = threadIdx.x & 31;
+    const int q0 = grp4(i0);
+    uint4 gA = radial_group(sp, q0, ray, pose);
+    uint4 gB = radial_group(sp, q0 + 1, ray, pose);
+    uint4 edge = make_uint4(0, 0, 0, 0);
+    if (lane == 0 || lane == 31) edge = radial_group(sp, lane == 0 ? q0 - 1 : q0 + 2, ray, pose);
+    uint4 gL = shfl_up_u4(gB, 1);
+    uint4 gR = shfl_down_u4(gA, 1);
+    if (lane == 0) gL = edge;
+    if (lane == 31) gR = edge;
+    float nu[16];
+    nu[0] = ih_normal(gL.x); nu[1] = ih_normal(gL.y); nu[2] = ih_normal(gL.z); nu[3] = ih_normal(gL.w);
+    nu[4] = ih_normal(gA.x); nu[5] = ih_normal(gA.y); nu[6] = ih_normal(gA.z); nu[7] = ih_normal(gA.w);
+    nu[8] = ih_normal(gB.x); nu[9] = ih_normal(gB.y); nu[10] = ih_normal(gB.z); nu[11] = ih_normal(gB.w);
+    nu[12] = ih_normal(gR.x); nu[13] = ih_normal(gR.y); nu[14] = ih_normal(gR.z); nu[15] = ih_normal(gR.w);
+    const int kb1 = (S + 3) / 4, kb2 = (2 * S + 3) / 4, kb3 = (3 * S + 3) / 4;
+    const float invS = 1.0f / (float)S;
+    uint32_t cur_grp = 0xffffffffu;
+    uint4 gw = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int t = 0; t < kChunk; t++) {
+        const int i = i0 + t;
+        m[t] = 1.0f;
+        if (i < S) {
+            float nr = 0.0f;
+#pragma unroll
+            for (int d = -4; d <= 4; d++) nr = fmaf(sp.wr[d + 4], nu[t + 4 + d], nr);
+            uint32_t cell = grain_cell(i, kb1, kb2, kb3, sp.gshift);
+            uint32_t grp = cell >> 2;
+            if (grp != cur_grp) {
+                gw = philox10(make_uint4(grp, (uint32_t)ray, pose, 1u), sp.key0, sp.key1);
+                cur_grp = grp;
+            }
+            float ng = ih_normal(pick4(gw, cell & 3u));
+            m[t] = speckle_factor(sp, (float)(i + 1) * invS, nr, ng);
+        }
+    }
+}
+
+// Forward march of one ray by one warp.  buf: this warp's shared row of
+// kSegPad floats.
+template <typename T>
+__device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, const RayGeo &rg,
+                              const RayOut &out, float *__restrict__ buf)
+{
+    const int lane = threadIdx.x & 31;
+    const int S = rg.S;
+    const uint32_t pose = A.sp.pose_ctr + (uint32_t)rg.pose;
+
+    float czr, cdz;
+    sample_z<T, false>(vol, A.g, rg.X0[0], rg.X0[1], rg.X0[2], czr, cdz);
+    float bs0 = 0.0f, bs1 = 1.0f, Ds = 1.0f;   // bottom row and det at segment start
+    int first_bad = 0x7fffffff;
+    int nonfinite = 0;
+    const bool vec4 = ((((uintptr_t)out.row) & 15) == 0);
+
+    for (int base = 0; base < S; base += kSeg) {
+        seg_reflections<T>(vol, A.g, rg, base, czr, cdz, buf);
+        __syncwarp();
+        const int i0 = base + lane * kChunk;
+        float rr[kChunk];
+#pragma unroll
+        for (int t = 0; t < kChunk; t++) rr[t] = buf[smem_idx(lane * kChunk + t)];
+        Mat2 Q, E, Qall;
+        float dq, de, dall;
+        chunk_product(rr, i0, S, A.a2, A.mode, Q, dq);
+        warp_scan_prefix(Q, dq, E, de, Qall, dall);
+        float b0 = fmaf(bs0, E.a, bs1 * E.c);
+        float b1 = fmaf(bs0, E.b, bs1 * E.d);
+        float D = Ds * de;
+        {
+            float n0 = fmaf(bs0, Qall.a, bs1 * Qall.c);
+            float n1 = fmaf(bs0, Qall.b, bs1 * Qall.d);
+            bs0 = n0;
+            bs1 = n1;
+            Ds *= dall;
+        }
+        float m[kChunk];
+        if (A.sp.on) {
+            chunk_speckle(A.sp, i0, S, rg.ray, pose, m);
+        } else {
+#pragma unroll
+            for (int t = 0; t < kChunk; t++) m[t] = 1.0f;
+        }
+        float y[kChunk];
+#pragma unroll
+        for (int t = 0; t < kChunk; t++) {
+            const int i = i0 + t;
+            y[t] = 0.0f;
+            if (i < S) {
+                Xfer x = xfer(rr[t], A.a2, A.mode);
+                float q = fmaf(b0, x.m01, b1);          // det(A_{i+1})
+                float e = x.m01 * D * __frcp_rn(b1 * q);
+                if (!(q >= kPoleEps)) first_bad = min(first_bad, i + 1);
+                float nb0 = fmaf(b0, x.m00, b1 * x.m10);
+                b1 = q;
+                b0 = nb0;
+                D *= x.delta;
+                y[t] = m[t] * e;
+                nonfinite += !isfinite(y[t]);
+            }
+        }
+        if (vec4 && i0 + kChunk <= S) {
+            float4 *dst = reinterpret_cast<float4 *>(out.row + i0);
+            dst[0] = make_float4(y[0], y[1], y[2], y[3]);
+            dst[1] = make_float4(y[4], y[5], y[6], y[7]);
+        } else {
+#pragma unroll
+            for (int t = 0; t < kChunk; t++)
+                if (i0 + t < S) out.row[i0 + t] = y[t];
+        }
+        __syncwarp();
+    }
+
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        first_bad = min(first_bad, __shfl_xor_sync(0xffffffffu, first_bad, off));
+        nonfinite += __shfl_xor_sync(0xffffffffu, nonfinite, off);
+    }
+    if (lane == 0) {
+        bool bad = first_bad <= S;
+        if (out.valid) out.valid[0] = bad ? first_bad - 1 : S;
+        if (out.status) {
+            if (bad) atomicAdd(out.status + 0, 1u);
+            if (nonfinite) atomicAdd(out.status + 1, (uint32_t)nonfinite);
+        }
+    }
+}
+
+}  // namespace dfs

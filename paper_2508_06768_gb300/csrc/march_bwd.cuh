@@ -1,0 +1,318 @@
+// Adjoint of the warp-per-ray march (reverse mode of Sections 2.3-2.4).
+//
+// For L = sum_i ge_i e_i with ge_i = speckle_i * dL/dy_i, the adjoint of the
+// bottom-row state (b_i, D_i) obeys
+//     lambda_i = de_i/db_i ge_i + lambda_{i+1} M_i^T,   mu_i = de_i/dD_i ge_i + mu_{i+1} delta_i,
+// an affine recurrence run from the end of the ray.  Each lane owns 8
+// interfaces of a 256-interface segment; the lanes' affine maps are combined
+// by a warp suffix scan, so the reverse sweep is as parallel as the forward
+// one.  Per-ray recomputation replaces stored march state: a forward sweep
+// keeps only the scan carry at each segment start (16 bytes per segment),
+// then segments are revisited from the last to the first.
+//
+// Outputs per ray: dL/dZ_k for the S+1 samples (for the volume gather) and
+// the ray's contribution to dL/dpose (FP64 sums of per-segment FP32 sums).
+#pragma once
+
+#include "march.cuh"
+
+namespace dfs {
+
+constexpr int kBwdPad = 289;   // smem_idx(256) + 1
+
+struct BwdSmem {
+    float zr[kBwdPad], dz[kBwdPad];   // samples base .. base+256 (zref + dz form)
+    float gx[kBwdPad], gy[kBwdPad], gz[kBwdPad];
+};
+
+// Echo of one interface and its partial derivatives with respect to the
+// state (b0, b1, D) and to x = m01 (see march.cuh for e).
+struct EchoGrad {
+    float gb0, gb1, gD, gx;
+};
+
+__device__ __forceinline__ EchoGrad echo_grad(float b0, float b1, float D, float x, float ge)
+{
+    if (ge == 0.0f) return {0.0f, 0.0f, 0.0f, 0.0f};   // masked rows (e.g. past a pole) add nothing
+    float q = fmaf(b0, x, b1);
+    float iq = __frcp_rn(q), ib1 = __frcp_rn(b1);
+    float e = x * D * ib1 * iq;
+    EchoGrad g;
+    g.gb0 = -ge * e * x * iq;
+    g.gb1 = -ge * e * (ib1 + iq);
+    g.gD = ge * x * ib1 * iq;
+    g.gx = ge * D * iq * iq;
+    return g;
+}
+
+template <typename T>
+__device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, const RayGeo &rg,
+                              const float *__restrict__ gy_row, float *__restrict__ gz_row,
+                              double *__restrict__ pose_part, float4 *__restrict__ ckpt, BwdSmem &sm)
+{
+    const int lane = threadIdx.x & 31;
+    const int S = rg.S;
+    const uint32_t pose = A.sp.pose_ctr + (uint32_t)rg.pose;
+    const int nseg = (S + kSeg - 1) / kSeg;
+    float *buf = sm.zr;   // sweep 1 uses the first array for reflection coefficients
+
+    // ---------------- sweep 1: forward, record the carry at segment starts
+    {
+        float czr, cdz;
+        sample_z<T, false>(vol, A.g, rg.X0[0], rg.X0[1], rg.X0[2], czr, cdz);
+        float bs0 = 0.0f, bs1 = 1.0f, Ds = 1.0f;
+        for (int s = 0; s < nseg; s++) {
+            const int base = s * kSeg;
+            if (lane == 0) ckpt[s] = make_float4(bs0, bs1, Ds, 0.0f);
+            seg_reflections<T>(vol, A.g, rg, base, czr, cdz, buf);
+            __syncwarp();
+            float rr[kChunk];
+#pragma unroll
+            for (int t = 0; t < kChunk; t++) rr[t] = buf[smem_idx(lane * kChunk + t)];
+            Mat2 Q, E, Qall;
+            float dq, de, dall;
+            chunk_product(rr, base + lane * kChunk, S, A.a2, A.mode, Q, dq);
+            warp_scan_prefix(Q, dq, E, de, Qall, dall);
+            float n0 = fmaf(bs0, Qall.a, bs1 * Qall.c);
+            float n1 = fmaf(bs0, Qall.b, bs1 * Qall.d);
+            bs0 = n0;
+            bs1 = n1;
+            Ds *= dall;
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+
+    // ---------------- sweep 2: reverse over segments
+    float lam0 = 0.0f, lam1 = 0.0f, mus = 0.0f;   // adjoint at the end of the current segment
+    float carry_gz1 = 0.0f;                       // dL/dZ of sample base+256 from interface base+256
+    float czr = 0.0f, cdz = 0.0f, cg0 = 0.0f, cg1 = 0.0f, cg2 = 0.0f;   // sample base+256
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const float ds = rg.ds;
+
+    for (int s = nseg - 1; s >= 0; s--) {
+        const int base = s * kSeg;
+        // A': samples base .. base+255 with gradients; sample base+256 carried
+#pragma unroll
+        for (int t = 0; t < kChunk; t++) {
+            int p = t * kWarp + lane;
+            int k = base + p;
+            float zr = 0.0f, dz = 0.0f, g3[3] = {0.0f, 0.0f, 0.0f};
+            if (k <= S) {
+                long long X, Y, Z;
+                sample_pos(rg, k, X, Y, Z);
+                sample_z<T, true>(vol, A.g, X, Y, Z, zr, dz, g3);
+            }
+            int o = smem_idx(p);
+            sm.zr[o] = zr; sm.dz[o] = dz; sm.gx[o] = g3[0]; sm.gy[o] = g3[1]; sm.gz[o] = g3[2];
+        }
+        if (lane == 0) {
+            if (s == nseg - 1 && base + kSeg <= S) {
+                long long X, Y, Z;
+                float g3[3];
+                sample_pos(rg, base + kSeg, X, Y, Z);
+                sample_z<T, true>(vol, A.g, X, Y, Z, czr, cdz, g3);
+                cg0 = g3[0]; cg1 = g3[1]; cg2 = g3[2];
+            }
+            int o = smem_idx(kSeg);
+            sm.zr[o] = czr; sm.dz[o] = cdz; sm.gx[o] = cg0; sm.gy[o] = cg1; sm.gz[o] = cg2;
+        }
+        __syncwarp();
+        {   // carry the first sample of this segment to the earlier one
+            int o = smem_idx(0);
+            czr = sm.zr[o]; cdz = sm.dz[o]; cg0 = sm.gx[o]; cg1 = sm.gy[o]; cg2 = sm.gz[o];
+        }
+
+        // B': reflection coefficients of this lane's chunk and the forward scan
+        const int i0 = base + lane * kChunk;
+        float rr[kChunk], Zs[kChunk + 1];
+#pragma unroll
+        for (int t = 0; t <= kChunk; t++) {
+            int o = smem_idx(lane * kChunk + t);
+            Zs[t] = sm.zr[o] + sm.dz[o];
+        }
+#pragma unroll
+        for (int t = 0; t < kChunk; t++) {
+            int o = smem_idx(lane * kChunk + t), o1 = smem_idx(lane * kChunk + t + 1);
+            rr[t] = (i0 + t < S) ? refl(sm.zr[o], sm.dz[o], sm.zr[o1], sm.dz[o1]) : 0.0f;
+        }
+        Mat2 Q, E, Qall;
+        float dq, de, dall;
+        chunk_product(rr, i0, S, A.a2, A.mode, Q, dq);
+        warp_scan_prefix(Q, dq, E, de, Qall, dall);
+        const float4 ck = ckpt[s];
+        float b0s[kChunk], b1s[kChunk], Dsv[kChunk];
+        {
+            float b0 = fmaf(ck.x, E.a, ck.y * E.c);
+            float b1 = fmaf(ck.x, E.b, ck.y * E.d);
+            float D = ck.z * de;
+#pragma unroll
+            for (int t = 0; t < kChunk; t++) {
+                b0s[t] = b0; b1s[t] = b1; Dsv[t] = D;
+                if (i0 + t < S) {
+                    Xfer x = xfer(rr[t], A.a2, A.mode);
+                    float nb0 = fmaf(b0, x.m00, b1 * x.m10);
+                    b1 = fmaf(b0, x.m01, b1);
+                    b0 = nb0;
+                    D *= x.delta;
+                }
+            }
+        }
+        // adjoint sources of the echo rows
+        float m[kChunk];
+        if (A.sp.on) {
+            chunk_speckle(A.sp, i0, S, rg.ray, pose, m);
+        } else {
+#pragma unroll
+            for (int t = 0; t < kChunk; t++) m[t] = 1.0f;
+        }
+        float ge[kChunk];
+#pragma unroll
+        for (int t = 0; t < kChunk; t++) ge[t] = (i0 + t < S) ? m[t] * __ldg(gy_row + i0 + t) : 0.0f;
+
+        // C': local reverse pass with zero adjoint at the chunk end
+        float c0 = 0.0f, c1 = 0.0f, dloc = 0.0f;
+#pragma unroll
+        for (int t = kChunk - 1; t >= 0; t--) {
+            if (i0 + t < S) {
+                Xfer x = xfer(rr[t], A.a2, A.mode);
+                EchoGrad g = echo_grad(b0s[t], b1s[t], Dsv[t], x.m01, ge[t]);
+                float n0 = g.gb0 + fmaf(c0, x.m00, c1 * x.m01);
+                float n1 = g.gb1 + fmaf(c0, x.m10, c1);
+                dloc = fmaf(dloc, x.delta, g.gD);
+                c0 = n0;
+                c1 = n1;
+            }
+        }
+        // D': warp suffix scan of the affine maps (lambda -> c + lambda Q^T, mu -> d + mu dq)
+        Mat2 Pm = Q;          // chunk product (warp_scan_prefix took Q by value)
+        float pal = dq;
+        float pc0 = c0, pc1 = c1, pd = dloc;
+#pragma unroll
+        for (int off = 1; off < kWarp; off <<= 1) {
+            Mat2 Po = {__shfl_down_sync(0xffffffffu, Pm.a, off), __shfl_down_sync(0xffffffffu, Pm.b, off),
+                       __shfl_down_sync(0xffffffffu, Pm.c, off), __shfl_down_sync(0xffffffffu, Pm.d, off)};
+            float o0 = __shfl_down_sync(0xffffffffu, pc0, off);
+            float o1 = __shfl_down_sync(0xffffffffu, pc1, off);
+            float oal = __shfl_down_sync(0xffffffffu, pal, off);
+            float od = __shfl_down_sync(0xffffffffu, pd, off);
+            if (lane + off < kWarp) {
+                // self o other: c + c_o P^T, P P_o ; d + d_o al, al al_o
+                float n0 = pc0 + fmaf(o0, Pm.a, o1 * Pm.b);
+                float n1 = pc1 + fmaf(o0, Pm.c, o1 * Pm.d);
+                pc0 = n0;
+                pc1 = n1;
+                pd = fmaf(od, pal, pd);
+                Pm = mat_mul(Pm, Po);
+                pal *= oal;
+            }
+        }
+        // adjoint at this lane's chunk end = G_{lane+1}(lambda_seg)
+        float le0, le1, lmu;
+        {
+            Mat2 Po = {__shfl_down_sync(0xffffffffu, Pm.a, 1), __shfl_down_sync(0xffffffffu, Pm.b, 1),
+                       __shfl_down_sync(0xffffffffu, Pm.c, 1), __shfl_down_sync(0xffffffffu, Pm.d, 1)};
+            float o0 = __shfl_down_sync(0xffffffffu, pc0, 1);
+            float o1 = __shfl_down_sync(0xffffffffu, pc1, 1);
+            float oal = __shfl_down_sync(0xffffffffu, pal, 1);
+            float od = __shfl_down_sync(0xffffffffu, pd, 1);
+            if (lane == kWarp - 1) {
+                le0 = lam0; le1 = lam1; lmu = mus;
+            } else {
+                le0 = o0 + fmaf(lam0, Po.a, lam1 * Po.b);
+                le1 = o1 + fmaf(lam0, Po.c, lam1 * Po.d);
+                lmu = fmaf(mus, oal, od);
+            }
+        }
+
+        // E': true reverse pass: parameter adjoints -> dL/dr -> dL/dZ
+        float gzc[kChunk], gzn[kChunk];
+        const float a2 = A.a2;
+#pragma unroll
+        for (int t = kChunk - 1; t >= 0; t--) {
+            gzc[t] = 0.0f;
+            gzn[t] = 0.0f;
+            if (i0 + t < S) {
+                const float r = rr[t];
+                Xfer x = xfer(r, a2, A.mode);
+                float gm00 = b0s[t] * le0, gm10 = b1s[t] * le0, gm01 = b0s[t] * le1;
+                float gdel = lmu * Dsv[t];
+                EchoGrad g = echo_grad(b0s[t], b1s[t], Dsv[t], x.m01, ge[t]);
+                float gr;
+                if (A.mode == DIFFUS_MODE_LITERAL) {
+                    float R = fabsf(r);
+                    float gR = gm00 * (-4.0f * a2 * R) + (gm01 + g.gx) * a2 - gm10 + gdel * (-2.0f * a2 * R);
+                    gr = r > 0.0f ? gR : (r < 0.0f ? -gR : 0.0f);
+                } else {
+                    gr = (gm01 + g.gx) * a2 + gm10 + gdel * (-2.0f * a2 * r);
+                }
+                float n0 = g.gb0 + fmaf(le0, x.m00, le1 * x.m01);
+                float n1 = g.gb1 + fmaf(le0, x.m10, le1);
+                lmu = fmaf(lmu, x.delta, g.gD);
+                le0 = n0;
+                le1 = n1;
+                float z1 = Zs[t], z2 = Zs[t + 1], sz = z1 + z2;
+                float is2 = __frcp_rn(sz * sz);
+                gzc[t] = gr * (-2.0f * z2) * is2;
+                gzn[t] = gr * (2.0f * z1) * is2;
+            }
+        }
+        // adjoint at the segment start for the earlier segment
+        lam0 = __shfl_sync(0xffffffffu, le0, 0);
+        lam1 = __shfl_sync(0xffffffffu, le1, 0);
+        mus = __shfl_sync(0xffffffffu, lmu, 0);
+
+        // F': finalise dL/dZ of samples i0+1 .. i0+8 (and sample 0)
+        float nextc = __shfl_down_sync(0xffffffffu, gzc[0], 1);
+        if (lane == kWarp - 1) nextc = carry_gz1;
+        float first_c = __shfl_sync(0xffffffffu, gzc[0], 0);
+        float a[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int t = 1; t <= kChunk; t++) {
+            int k = i0 + t;
+            float G = (t < kChunk) ? gzc[t] + gzn[t - 1] : gzn[kChunk - 1] + nextc;
+            if (k <= S) {
+                gz_row[k] = G;
+                int o = smem_idx(lane * kChunk + t);
+                float gx = sm.gx[o], gyv = sm.gy[o], gzv = sm.gz[o];
+                float sk = ((float)k + 0.5f) * ds;
+                a[0] = fmaf(G, gx, a[0]);
+                a[1] = fmaf(G, gyv, a[1]);
+                a[2] = fmaf(G, gzv, a[2]);
+                a[3] = fmaf(G * sk, gx, a[3]);
+                a[4] = fmaf(G * sk, gyv, a[4]);
+                a[5] = fmaf(G * sk, gzv, a[5]);
+            }
+        }
+        if (s == 0 && lane == 0) {
+            float G = gzc[0];
+            gz_row[0] = G;
+            int o = smem_idx(0);
+            float sk = 0.5f * ds;
+            a[0] = fmaf(G, sm.gx[o], a[0]);
+            a[1] = fmaf(G, sm.gy[o], a[1]);
+            a[2] = fmaf(G, sm.gz[o], a[2]);
+            a[3] = fmaf(G * sk, sm.gx[o], a[3]);
+            a[4] = fmaf(G * sk, sm.gy[o], a[4]);
+            a[5] = fmaf(G * sk, sm.gz[o], a[5]);
+        }
+        carry_gz1 = first_c;
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+            float v = a[q];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            acc[q] += (double)v;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        pose_part[0] = acc[0];
+        pose_part[1] = acc[1];
+        pose_part[2] = acc[2];
+        for (int q = 0; q < 3; q++)
+            pose_part[3 + q] = acc[3] * (double)rg.v[q][0] + acc[4] * (double)rg.v[q][1] + acc[5] * (double)rg.v[q][2];
+    }
+}
+
+}  // namespace dfs

@@ -1,0 +1,110 @@
+// Single-pose forward entry point: ray setup -> warp-per-ray march -> blur.
+#include "host.hpp"
+
+using namespace dfs;
+
+namespace {
+
+struct FwdLayout {
+    RayGeo *geo;
+    float *y;       // pre-blur echo rows (only when blurring)
+    size_t bytes;
+};
+
+FwdLayout fwd_layout(void *ws, const diffus_fan *fan, const diffus_params *prm)
+{
+    Carve c(ws);
+    FwdLayout L;
+    L.geo = c.take<RayGeo>((size_t)fan->n_rays);
+    L.y = prm->blur ? c.take<float>((size_t)fan->n_rays * fan->n_samples) : nullptr;
+    L.bytes = c.used;
+    return L;
+}
+
+}  // namespace
+
+namespace dfs {
+
+size_t fwd_workspace_bytes(const diffus_fan *fan, const diffus_params *prm)
+{
+    return fwd_layout(nullptr, fan, prm).bytes;
+}
+
+MarchArgs make_march_args(const diffus_volume_desc *vd, const diffus_fan *fan, const diffus_params *prm)
+{
+    MarchArgs A;
+    A.g = make_volgeo(vd);
+    double a = attenuation_a(fan);
+    A.a2 = (float)(a * a);
+    A.mode = prm->mode;
+    A.sp = make_speckle(prm);
+    return A;
+}
+
+int check_common(const void *vol, const diffus_volume_desc *vd, const float *pose, const diffus_fan *fan,
+                 const diffus_params *prm)
+{
+    int rc;
+    if ((rc = check_vol(vd))) return rc;
+    if ((rc = check_fan(fan, vd))) return rc;
+    if ((rc = check_params(prm))) return rc;
+    if (!vol || !pose) return DIFFUS_E_NULL;
+    size_t el = vd->dtype == DIFFUS_F32 ? 4 : 2;
+    if (((uintptr_t)vol) % el || ((uintptr_t)pose) % 4) return DIFFUS_E_ALIGN;
+    return DIFFUS_OK;
+}
+
+// Launches ray setup and the march for one pose into `out` (pre-blur rows
+// when blurring follows).
+int launch_fwd_march(const void *vol, const diffus_volume_desc *vd, const float *pose, const diffus_fan *fan,
+                     const diffus_params *prm, RayGeo *geo, float *out, int32_t *ray_valid, uint32_t *status,
+                     cudaStream_t s)
+{
+    FanDev fd{fan->n_rays, fan->n_samples, fan->fov_rad, fan->depth_mm};
+    k_ray_setup<<<(fan->n_rays + 127) / 128, 128, 0, s>>>(pose, fd, make_place(vd), geo);
+    MarchArgs A = make_march_args(vd, fan, prm);
+    int grid = (fan->n_rays + kWarpsFwd - 1) / kWarpsFwd;
+    if (vd->dtype == DIFFUS_F32)
+        k_march_fwd<float><<<grid, kWarpsFwd * 32, 0, s>>>((const float *)vol, A, geo, fan->n_rays, out,
+                                                           ray_valid, status);
+    else
+        k_march_fwd<unsigned short><<<grid, kWarpsFwd * 32, 0, s>>>((const unsigned short *)vol, A, geo,
+                                                                    fan->n_rays, out, ray_valid, status);
+    return launch_status();
+}
+
+int launch_blur(const float *in, float *out, int n, int S, const diffus_params *prm, bool transpose,
+                cudaStream_t s)
+{
+    BlurArgs b{(float)prm->sigma0, (float)prm->sigma1, blur_halfwidth(prm)};
+    dim3 grid((S + kBlurRows - 1) / kBlurRows, (n + kBlurRays - 1) / kBlurRays);
+    size_t sm = blur_smem_bytes(b.W);
+    if (transpose)
+        k_blur<true><<<grid, kBlurThreads, sm, s>>>(in, out, n, S, b);
+    else
+        k_blur<false><<<grid, kBlurThreads, sm, s>>>(in, out, n, S, b);
+    return launch_status();
+}
+
+}  // namespace dfs
+
+extern "C" int diffus_render_fwd(const void *vol, const diffus_volume_desc *vd, const float *pose,
+                                 const diffus_fan *fan, const diffus_params *prm, float *image,
+                                 int32_t *ray_valid, uint32_t *status, void *workspace, size_t ws_bytes,
+                                 diffus_stream_t stream)
+{
+    int rc = check_common(vol, vd, pose, fan, prm);
+    if (rc) return rc;
+    if (!image) return DIFFUS_E_NULL;
+    if (((uintptr_t)image) % 4 || (ray_valid && ((uintptr_t)ray_valid) % 4) || (status && ((uintptr_t)status) % 4))
+        return DIFFUS_E_ALIGN;
+    FwdLayout L = fwd_layout(workspace, fan, prm);
+    if (!workspace || ws_bytes < L.bytes) return DIFFUS_E_WORKSPACE;
+    if (((uintptr_t)workspace) % 256) return DIFFUS_E_ALIGN;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (status && cudaMemsetAsync(status, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
+    float *march_out = prm->blur ? L.y : image;
+    if ((rc = launch_fwd_march(vol, vd, pose, fan, prm, L.geo, march_out, ray_valid, status, s))) return rc;
+    if (prm->blur) rc = launch_blur(L.y, image, fan->n_rays, fan->n_samples, prm, false, s);
+    return rc;
+}
