@@ -158,9 +158,10 @@ int diffus_render_bwd(const void *vol, const diffus_volume_desc *vd, const float
 
 /* Launch schedule of the batched path.  rays_per_cta: warps (one ray each)
  * per CTA of the persistent marches (2, 4 or 8); ctas_per_sm: resident CTAs
- * per SM used to size the persistent grid; brick: poses per chunk of the
- * volume-gradient gather (each chunk is one launch over the touched 8^3
- * bricks).  Zero fields take defaults (4, 4, 16). */
+ * per SM used to size the persistent march grids; brick: CTAs per SM of the
+ * volume-gradient gather grid (1..64).  Zero fields take defaults (4, 4, 8).
+ * The schedule changes the launch shapes only, never the arithmetic of a
+ * ray or a brick. */
 typedef struct {
     int32_t rays_per_cta;
     int32_t ctas_per_sm;

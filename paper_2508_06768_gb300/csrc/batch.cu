@@ -10,7 +10,6 @@
 #include <numeric>
 #include <vector>
 
-#include "gather.cuh"
 #include "host.hpp"
 #include "march_bwd.cuh"
 
@@ -18,9 +17,10 @@ using namespace dfs;
 
 namespace dfs {
 MarchArgs make_march_args(const diffus_volume_desc *vd, const diffus_fan *fan, const diffus_params *prm);
-int launch_gather(const diffus_volume_desc *vd, const float *poses, const double *depth_dev, double depth_all,
-                  int P, int pose_chunk, const RayGeo *geo, const int *ray0, const float *gz, const long long *gz_off,
-                  PoseBox *boxes, int *list, int *count, float *grad_vol, cudaStream_t s);
+size_t gather_workspace_bytes(const diffus_volume_desc *vd, long long n_rays, double max_path_mm);
+int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_rays, double max_path_mm,
+                  const float *gz, const long long *gz_off, void *ws, uint32_t *status, float *grad_vol,
+                  int ctas_per_sm, cudaStream_t s);
 }  // namespace dfs
 
 namespace {
@@ -43,8 +43,9 @@ struct PlanHeader {
     uint32_t magic;
     int32_t P;
     int64_t total_rays, total_img, total_gz, total_ckpt, n_tiles;
+    double max_depth;
     int32_t max_S, blurW;
-    int32_t warps, ctas_per_sm, pose_chunk, brick;
+    int32_t warps, ctas_per_sm, gather_ctas, pad_;
     int64_t off_pose, off_depth, off_ray0, off_ray_pose, off_ray_j, off_order, off_row_off, off_gz_off, off_ck_off,
         off_tiles;
     int64_t bytes;
@@ -113,8 +114,7 @@ struct BatchLayout {
     float *gz;
     double *part;
     float4 *ckpt;
-    PoseBox *boxes;
-    int *list, *count;
+    void *gather_ws;
     size_t fwd_bytes, bytes;
 };
 
@@ -126,15 +126,11 @@ BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc
     L.counter = c.take<unsigned>(4);
     L.y = blur ? c.take<float>((size_t)H.total_img) : nullptr;
     L.fwd_bytes = c.used;
-    size_t nb = (size_t)((vd->nx + kBrick - 1) / kBrick) * ((vd->ny + kBrick - 1) / kBrick) *
-                ((vd->nz + kBrick - 1) / kBrick);
     L.gy = blur ? c.take<float>((size_t)H.total_img) : nullptr;
     L.gz = c.take<float>((size_t)H.total_gz);
     L.part = c.take<double>(6 * (size_t)H.total_rays);
     L.ckpt = c.take<float4>((size_t)H.total_ckpt);
-    L.boxes = c.take<PoseBox>((size_t)H.P);
-    L.list = c.take<int>(nb);
-    L.count = c.take<int>(1);
+    L.gather_ws = (void *)c.take<char>(gather_workspace_bytes(vd, H.total_rays, H.max_depth));
     L.bytes = c.used;
     return L;
 }
@@ -319,6 +315,7 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     if (P < 1) return DIFFUS_E_DIMS;
     int64_t total_rays = 0, total_img = 0, total_gz = 0, total_ck = 0;
     int max_S = 0;
+    double max_depth = 0.0;
     for (int p = 0; p < P; p++) {
         if ((rc = check_fan(&fans[p], vd))) return rc;
         total_rays += fans[p].n_rays;
@@ -326,6 +323,7 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
         total_gz += (int64_t)fans[p].n_rays * (fans[p].n_samples + 1);
         total_ck += (int64_t)fans[p].n_rays * ((fans[p].n_samples + kSeg - 1) / kSeg);
         max_S = std::max(max_S, (int)fans[p].n_samples);
+        max_depth = std::max(max_depth, fans[p].depth_mm);
     }
     if (total_rays > INT32_MAX) return DIFFUS_E_DIMS;
     const int64_t n_tiles = count_tiles(fans, P);
@@ -335,9 +333,9 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     diffus_schedule sc = sched ? *sched : diffus_schedule{0, 0, 0, 0};
     if (sc.rays_per_cta == 0) sc.rays_per_cta = 4;
     if (sc.ctas_per_sm == 0) sc.ctas_per_sm = 4;
-    if (sc.brick == 0) sc.brick = 16;   // poses per gather chunk
+    if (sc.brick == 0) sc.brick = 8;    // gather CTAs per SM
     if (sc.rays_per_cta != 2 && sc.rays_per_cta != 4 && sc.rays_per_cta != 8) return DIFFUS_E_PARAM;
-    if (sc.ctas_per_sm < 1 || sc.ctas_per_sm > 32 || sc.brick < 1) return DIFFUS_E_PARAM;
+    if (sc.ctas_per_sm < 1 || sc.ctas_per_sm > 32 || sc.brick < 1 || sc.brick > 64) return DIFFUS_E_PARAM;
 
     memset(plan_host, 0, (size_t)z.bytes);
     PlanHeader &H = *(PlanHeader *)plan_host;
@@ -349,11 +347,11 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     H.total_ckpt = total_ck;
     H.n_tiles = n_tiles;
     H.max_S = max_S;
+    H.max_depth = max_depth;
     H.blurW = blur_halfwidth(prm);
     H.warps = sc.rays_per_cta;
     H.ctas_per_sm = sc.ctas_per_sm;
-    H.pose_chunk = sc.brick;
-    H.brick = kBrick;
+    H.gather_ctas = sc.brick;
     H.off_pose = z.off[0]; H.off_depth = z.off[1]; H.off_ray0 = z.off[2]; H.off_ray_pose = z.off[3];
     H.off_ray_j = z.off[4]; H.off_order = z.off[5]; H.off_row_off = z.off[6]; H.off_gz_off = z.off[7];
     H.off_ck_off = z.off[8]; H.off_tiles = z.off[9];
@@ -429,8 +427,15 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     BatchLayout L = batch_layout(workspace, H, vd, prm->blur != 0);
     if (ws_bytes < (bwd ? L.bytes : L.fwd_bytes)) return DIFFUS_E_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (trace && cudaStreamIsCapturing(s, &cap) != cudaSuccess) return DIFFUS_E_LAUNCH;
     auto mark = [&](int i) {
-        if (trace && trace->event[i]) cudaEventRecord((cudaEvent_t)trace->event[i], s);
+        if (!trace || !trace->event[i]) return;
+        // inside a capture an external record becomes an event-record node of the graph
+        if (cap == cudaStreamCaptureStatusActive)
+            cudaEventRecordWithFlags((cudaEvent_t)trace->event[i], s, cudaEventRecordExternal);
+        else
+            cudaEventRecord((cudaEvent_t)trace->event[i], s);
     };
 
     BatchDev B;
@@ -493,8 +498,8 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     if (grad_poses) k_pose_reduce_batch<<<(H.P + 3) / 4, 128, 0, s>>>(L.part, ray0, H.P, grad_poses);
     mark(DIFFUS_TR_GATHER);
     if (grad_vol)
-        rc = launch_gather(vd, poses, at<double>(plan_dev, H.off_depth), 0.0, H.P, H.pose_chunk, L.geo, ray0, L.gz,
-                           (const long long *)B.gz_off, L.boxes, L.list, L.count, grad_vol, s);
+        rc = launch_gather(vd, L.geo, H.total_rays, H.max_depth, L.gz, (const long long *)B.gz_off, L.gather_ws,
+                           status, grad_vol, H.gather_ctas, s);
     mark(DIFFUS_TR_END);
     return rc ? rc : launch_status();
 }

@@ -1,0 +1,428 @@
+// Volume-gradient gather: brick runs, stable radix sort, units, reduction.
+// See gather.cuh for the algorithm.
+#include "gather.cuh"
+#include "host.hpp"
+
+namespace dfs {
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;                  // items per thread per tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kScanChunk = 4096;
+
+// ------------------------------------------------------------------ runs
+
+__global__ void k_ray_runs(const RayGeo *__restrict__ geo, int n_rays, GatherArgs G, int cap, uint32_t sentinel,
+                           Run *__restrict__ runs, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                           uint32_t *__restrict__ status)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const RayGeo rg = geo[r];
+    const long long S = rg.S;
+    const int n[3] = {G.nx, G.ny, G.nz};
+    int b[3];
+    long long nxt[3];
+    for (int a = 0; a < 3; a++) {
+        b[a] = cell_of(rg.X0[a], n[a]) / kBrick;
+        nxt[a] = next_change(rg.X0[a], rg.DX[a], b[a], n[a], S);
+    }
+    long long k = 0;
+    int cnt = 0;
+    const size_t base = (size_t)r * cap;
+    while (k <= S) {
+        long long kn = nxt[0];
+        kn = nxt[1] < kn ? nxt[1] : kn;
+        kn = nxt[2] < kn ? nxt[2] : kn;
+        long long k1 = kn - 1 < S ? kn - 1 : S;
+        if (cnt < cap) {
+            const uint32_t brick = (uint32_t)((b[2] * G.nby + b[1]) * G.nbx + b[0]);
+            runs[base + cnt] = Run{r, (int)k, (int)k1, (int)brick};
+            keys[base + cnt] = brick;
+            vals[base + cnt] = (uint32_t)(base + cnt);
+            cnt++;
+        } else if (status) {
+            atomicOr(status + 2, (uint32_t)DIFFUS_STATUS_QUEUE);
+        }
+        k = kn;
+        if (k > S) break;
+        for (int a = 0; a < 3; a++) {
+            if (nxt[a] == kn) {
+                long long X = rg.X0[a] + k * rg.DX[a];
+                b[a] = cell_of(X, n[a]) / kBrick;
+                nxt[a] = next_change(rg.X0[a], rg.DX[a], b[a], n[a], S);
+                if (nxt[a] <= k) nxt[a] = k + 1;   // guard: never stall
+            }
+        }
+    }
+    for (int i = cnt; i < cap; i++) {
+        keys[base + i] = sentinel;
+        vals[base + i] = (uint32_t)(base + i);
+    }
+}
+
+// ------------------------------------------------------------ exclusive scan
+
+__global__ void k_chunk_sums(const uint32_t *__restrict__ in, size_t n, uint32_t *__restrict__ sums)
+{
+    __shared__ uint32_t red[32];
+    const size_t b0 = (size_t)blockIdx.x * kScanChunk;
+    uint32_t s = 0;
+    for (int i = threadIdx.x; i < kScanChunk; i += blockDim.x)
+        if (b0 + i < n) s += in[b0 + i];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (threadIdx.x == 0) sums[blockIdx.x] = v;
+    }
+}
+
+// single block: exclusive scan of m values in place, total to *total
+__global__ void k_scan_sums(uint32_t *__restrict__ sums, int m, uint32_t *__restrict__ total)
+{
+    __shared__ uint32_t buf[1024];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < m; base += 1024) {
+        int i = base + threadIdx.x;
+        uint32_t v = i < m ? sums[i] : 0;
+        buf[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            uint32_t t = threadIdx.x >= off ? buf[threadIdx.x - off] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += t;
+            __syncthreads();
+        }
+        uint32_t incl = buf[threadIdx.x];
+        if (i < m) sums[i] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void k_chunk_scan(const uint32_t *__restrict__ in, size_t n, const uint32_t *__restrict__ sums,
+                             uint32_t *__restrict__ out)
+{
+    __shared__ uint32_t buf[1024];
+    __shared__ uint32_t carry;
+    const size_t b0 = (size_t)blockIdx.x * kScanChunk;
+    if (threadIdx.x == 0) carry = sums[blockIdx.x];
+    __syncthreads();
+    for (int base = 0; base < kScanChunk; base += 1024) {
+        size_t i = b0 + base + threadIdx.x;
+        uint32_t v = i < n ? in[i] : 0;
+        buf[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < 1024; off <<= 1) {
+            uint32_t t = threadIdx.x >= off ? buf[threadIdx.x - off] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += t;
+            __syncthreads();
+        }
+        uint32_t incl = buf[threadIdx.x];
+        if (i < n) out[i] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += incl;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------- stable radix sort
+
+__global__ void k_digit_hist(const uint32_t *__restrict__ keys, size_t n, int shift, int nblk,
+                             uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const size_t b0 = (size_t)blockIdx.x * kSortTile;
+    for (int s = 0; s < kSortItems; s++) {
+        size_t i = b0 + (size_t)s * kSortThreads + threadIdx.x;
+        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);   // integer counts: order-free
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter: an item's position is its digit's offset for this tile,
+// plus the items of the same digit earlier in the tile (earlier sub-tiles,
+// earlier warps, lower lanes).
+__global__ void __launch_bounds__(kSortThreads) k_digit_scatter(const uint32_t *__restrict__ kin,
+                                                                const uint32_t *__restrict__ vin, size_t n, int shift,
+                                                                int nblk, const uint32_t *__restrict__ offs,
+                                                                uint32_t *__restrict__ kout,
+                                                                uint32_t *__restrict__ vout)
+{
+    constexpr int W = kSortThreads / 32;
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t wcnt[W][257];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    run[threadIdx.x] = offs[(size_t)threadIdx.x * nblk + blockIdx.x];
+    for (int q = 0; q < W; q++) wcnt[q][threadIdx.x] = 0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < W; q++) wcnt[q][256] = 0;
+    __syncthreads();
+    const size_t b0 = (size_t)blockIdx.x * kSortTile;
+    for (int s = 0; s < kSortItems; s++) {
+        const size_t i = b0 + (size_t)s * kSortThreads + threadIdx.x;
+        const bool valid = i < n;
+        const uint32_t key = valid ? kin[i] : 0u;
+        const uint32_t val = valid ? vin[i] : 0u;
+        const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int wrank = __popc(peers & ((1u << lane) - 1u));
+        if (wrank == 0) wcnt[w][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = run[d] + (uint32_t)wrank;
+            for (int q = 0; q < w; q++) pos += wcnt[q][d];
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        uint32_t add = 0;
+        for (int q = 0; q < W; q++) {
+            add += wcnt[q][threadIdx.x];
+            wcnt[q][threadIdx.x] = 0;
+        }
+        run[threadIdx.x] += add;
+        if (threadIdx.x == 0)
+            for (int q = 0; q < W; q++) wcnt[q][256] = 0;
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------------- units
+
+// brick -> [start, end) of its runs in the sorted order
+__global__ void k_brick_bounds(const uint32_t *__restrict__ keys, size_t n, uint32_t sentinel,
+                               uint32_t *__restrict__ bstart, uint32_t *__restrict__ bend)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k = keys[i];
+    if (k == sentinel) return;
+    if (i == 0 || keys[i - 1] != k) bstart[k] = (uint32_t)i;
+    if (i + 1 == n || keys[i + 1] != k) bend[k] = (uint32_t)(i + 1);
+}
+
+__global__ void k_unit_counts(const uint32_t *__restrict__ bstart, const uint32_t *__restrict__ bend, int nb,
+                              uint32_t *__restrict__ ucount)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    uint32_t c = bend[b] - bstart[b];
+    ucount[b] = (c + kUnitRuns - 1) / kUnitRuns;
+}
+
+// One CTA per unit (grid-stride): gather the unit's runs into its 9^3 partial.
+__global__ void __launch_bounds__(kGatherWarps * 32)
+    k_gather_units(const RayGeo *__restrict__ geo, const float *__restrict__ gz, const long long *__restrict__ gz_off,
+                   const Run *__restrict__ runs, const uint32_t *__restrict__ sorted_vals,
+                   const uint32_t *__restrict__ bstart, const uint32_t *__restrict__ bend,
+                   const uint32_t *__restrict__ ustart, const uint32_t *__restrict__ n_units, int nb, GatherArgs G,
+                   float *__restrict__ upart)
+{
+    __shared__ GatherSmem sm;
+    const int w = threadIdx.x >> 5;
+    const uint32_t total = *n_units;
+    for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
+        // brick of unit u: last b with ustart[b] <= u
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (ustart[mid] <= u) lo = mid; else hi = mid - 1;
+        }
+        const int b = lo;
+        const uint32_t part = u - ustart[b];
+        const uint32_t r0 = bstart[b] + part * kUnitRuns;
+        uint32_t r1 = r0 + kUnitRuns;
+        r1 = r1 < bend[b] ? r1 : bend[b];
+        const int bx0 = (b % G.nbx) * kBrick, by0 = ((b / G.nbx) % G.nby) * kBrick, bz0 = (b / (G.nbx * G.nby)) * kBrick;
+        for (int i = threadIdx.x; i < kGatherWarps * kBrickVox; i += blockDim.x) (&sm.acc[0][0])[i] = 0.0f;
+        __syncthreads();
+        for (uint32_t q = r0 + w; q < r1; q += kGatherWarps) {
+            const Run run = runs[sorted_vals[q]];
+            const RayGeo rg = geo[run.ray];
+            gather_run(rg, gz + gz_off[run.ray], G, run.k0, run.k1, bx0, by0, bz0, sm, w);
+        }
+        __syncthreads();
+        float *out = upart + (size_t)u * kBrickVox;
+        for (int v = threadIdx.x; v < kBrickVox; v += blockDim.x) {
+            float s = sm.acc[0][v];
+#pragma unroll
+            for (int q = 1; q < kGatherWarps; q++) s += sm.acc[q][v];
+            out[v] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// Each voxel: sum over the bricks whose cells touch it (brick of cell v and,
+// on a brick face, of cell v-1), units in order.
+__global__ void k_voxel_reduce(const float *__restrict__ upart, const uint32_t *__restrict__ ustart,
+                               const uint32_t *__restrict__ ucount, GatherArgs G, float *__restrict__ grad_vol)
+{
+    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nv = (size_t)G.nx * G.ny * G.nz;
+    if (v >= nv) return;
+    const int vx = (int)(v % G.nx), vy = (int)((v / G.nx) % G.ny), vz = (int)(v / ((size_t)G.nx * G.ny));
+    float s = 0.0f;
+    for (int dz = 1; dz >= 0; dz--) {
+        int cz = vz - dz;                         // a cell of the brick, touching voxel vz
+        if (cz < 0 || cz > G.nz - 2) continue;
+        int bz = cz / kBrick;
+        if (dz == 1 && bz == vz / kBrick && vz <= G.nz - 2) continue;   // same brick counted with dz = 0
+        for (int dy = 1; dy >= 0; dy--) {
+            int cy = vy - dy;
+            if (cy < 0 || cy > G.ny - 2) continue;
+            int by = cy / kBrick;
+            if (dy == 1 && by == vy / kBrick && vy <= G.ny - 2) continue;
+            for (int dx = 1; dx >= 0; dx--) {
+                int cx = vx - dx;
+                if (cx < 0 || cx > G.nx - 2) continue;
+                int bx = cx / kBrick;
+                if (dx == 1 && bx == vx / kBrick && vx <= G.nx - 2) continue;
+                const int b = (bz * G.nby + by) * G.nbx + bx;
+                const int li = ((vz - bz * kBrick) * kBrickV + (vy - by * kBrick)) * kBrickV + (vx - bx * kBrick);
+                const uint32_t u0 = ustart[b], u1 = u0 + ucount[b];
+                for (uint32_t u = u0; u < u1; u++) s += upart[(size_t)u * kBrickVox + li];
+            }
+        }
+    }
+    grad_vol[v] = s;
+}
+
+int sort_bits(int nb)
+{
+    int bits = 1;
+    while ((1u << bits) <= (uint32_t)nb) bits++;   // sentinel (2^bits - 1) > every brick id
+    return bits;
+}
+
+}  // namespace
+
+GatherArgs make_gather_args(const diffus_volume_desc *vd)
+{
+    GatherArgs G;
+    G.nx = vd->nx; G.ny = vd->ny; G.nz = vd->nz;
+    G.nbx = (vd->nx - 2) / kBrick + 1;
+    G.nby = (vd->ny - 2) / kBrick + 1;
+    G.nbz = (vd->nz - 2) / kBrick + 1;
+    return G;
+}
+
+// Upper bound on the brick runs of one ray: the brick index is monotone on
+// every axis and moves at most ceil(S ds / (8 s_a)) + 1 bricks on axis a.
+int runs_per_ray(const diffus_volume_desc *vd, double max_path_mm)
+{
+    GatherArgs G = make_gather_args(vd);
+    int nb[3] = {G.nbx, G.nby, G.nbz};
+    double sp[3] = {vd->sx, vd->sy, vd->sz};
+    int cap = 1;
+    for (int a = 0; a < 3; a++) {
+        double m = ceil(max_path_mm / (kBrick * sp[a])) + 1.0;
+        cap += (int)fmin((double)(nb[a] - 1), m);
+    }
+    return cap;
+}
+
+struct GatherLayout {
+    Run *runs;
+    uint32_t *keys[2], *vals[2];
+    uint32_t *hist, *sums, *misc;   // misc: [0] units total, [1] scan total
+    uint32_t *bstart, *bend, *ucount, *ustart;
+    float *upart;
+    size_t bytes;
+};
+
+static GatherLayout gather_layout(void *ws, const diffus_volume_desc *vd, long long n_rays, int cap)
+{
+    Carve c(ws);
+    GatherLayout L;
+    GatherArgs G = make_gather_args(vd);
+    size_t nb = (size_t)G.nbx * G.nby * G.nbz;
+    size_t slots = (size_t)n_rays * cap;
+    size_t nblk = (slots + kSortTile - 1) / kSortTile;
+    size_t nhist = 256 * nblk;
+    size_t nsums = (std::max(nhist, nb) + kScanChunk - 1) / kScanChunk;
+    size_t max_units = slots / kUnitRuns + nb;
+    L.runs = c.take<Run>(slots);
+    L.keys[0] = c.take<uint32_t>(slots);
+    L.keys[1] = c.take<uint32_t>(slots);
+    L.vals[0] = c.take<uint32_t>(slots);
+    L.vals[1] = c.take<uint32_t>(slots);
+    L.hist = c.take<uint32_t>(nhist);
+    L.sums = c.take<uint32_t>(nsums + 1);
+    L.misc = c.take<uint32_t>(4);
+    L.bstart = c.take<uint32_t>(nb);
+    L.bend = c.take<uint32_t>(nb);
+    L.ucount = c.take<uint32_t>(nb);
+    L.ustart = c.take<uint32_t>(nb);
+    L.upart = c.take<float>(max_units * kBrickVox);
+    L.bytes = c.used;
+    return L;
+}
+
+size_t gather_workspace_bytes(const diffus_volume_desc *vd, long long n_rays, double max_path_mm)
+{
+    return gather_layout(nullptr, vd, n_rays, runs_per_ray(vd, max_path_mm)).bytes;
+}
+
+static void launch_scan(const uint32_t *in, uint32_t *out, size_t n, uint32_t *sums, uint32_t *total, cudaStream_t s)
+{
+    int nch = (int)((n + kScanChunk - 1) / kScanChunk);
+    k_chunk_sums<<<nch, 256, 0, s>>>(in, n, sums);
+    k_scan_sums<<<1, 1024, 0, s>>>(sums, nch, total);
+    k_chunk_scan<<<nch, 1024, 0, s>>>(in, n, sums, out);
+}
+
+int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_rays, double max_path_mm,
+                  const float *gz, const long long *gz_off, void *ws, uint32_t *status, float *grad_vol,
+                  int ctas_per_sm, cudaStream_t s)
+{
+    const GatherArgs G = make_gather_args(vd);
+    const int nb = G.nbx * G.nby * G.nbz;
+    const int cap = runs_per_ray(vd, max_path_mm);
+    GatherLayout L = gather_layout(ws, vd, n_rays, cap);
+    const size_t slots = (size_t)n_rays * cap;
+    const int bits = sort_bits(nb);
+    const uint32_t sentinel = (1u << bits) - 1u;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+
+    k_ray_runs<<<(unsigned)((n_rays + 127) / 128), 128, 0, s>>>(geo, (int)n_rays, G, cap, sentinel, L.runs, L.keys[0],
+                                                               L.vals[0], status);
+    // stable LSD radix sort by brick
+    const int nblk = (int)((slots + kSortTile - 1) / kSortTile);
+    int cur = 0;
+    for (int shift = 0; shift < bits; shift += 8) {
+        k_digit_hist<<<nblk, kSortThreads, 0, s>>>(L.keys[cur], slots, shift, nblk, L.hist);
+        launch_scan(L.hist, L.hist, (size_t)256 * nblk, L.sums, L.misc + 1, s);
+        k_digit_scatter<<<nblk, kSortThreads, 0, s>>>(L.keys[cur], L.vals[cur], slots, shift, nblk, L.hist,
+                                                      L.keys[cur ^ 1], L.vals[cur ^ 1]);
+        cur ^= 1;
+    }
+    if (cudaMemsetAsync(L.bstart, 0, sizeof(uint32_t) * nb, s) != cudaSuccess) return DIFFUS_E_LAUNCH;
+    if (cudaMemsetAsync(L.bend, 0, sizeof(uint32_t) * nb, s) != cudaSuccess) return DIFFUS_E_LAUNCH;
+    k_brick_bounds<<<(unsigned)((slots + 255) / 256), 256, 0, s>>>(L.keys[cur], slots, sentinel, L.bstart, L.bend);
+    k_unit_counts<<<(nb + 255) / 256, 256, 0, s>>>(L.bstart, L.bend, nb, L.ucount);
+    launch_scan(L.ucount, L.ustart, (size_t)nb, L.sums, L.misc + 0, s);
+    k_gather_units<<<sms * ctas_per_sm, kGatherWarps * 32, 0, s>>>(geo, gz, gz_off, L.runs, L.vals[cur], L.bstart, L.bend,
+                                                         L.ustart, L.misc + 0, nb, G, L.upart);
+    const size_t nv = (size_t)vd->nx * vd->ny * vd->nz;
+    k_voxel_reduce<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(L.upart, L.ustart, L.ucount, G, grad_vol);
+    return launch_status();
+}
+
+}  // namespace dfs

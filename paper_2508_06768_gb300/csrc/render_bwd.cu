@@ -1,6 +1,5 @@
 // Single-pose backward entry point: blur transpose -> adjoint march ->
 // pose reduction -> atomic-free brick gather of the volume gradient.
-#include "gather.cuh"
 #include "host.hpp"
 #include "march_bwd.cuh"
 
@@ -9,6 +8,10 @@ using namespace dfs;
 namespace dfs {
 
 int launch_blur(const float *in, float *out, int n, int S, const diffus_params *prm, bool transpose, cudaStream_t s);
+size_t gather_workspace_bytes(const diffus_volume_desc *vd, long long n_rays, double max_path_mm);
+int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_rays, double max_path_mm,
+                  const float *gz, const long long *gz_off, void *ws, uint32_t *status, float *grad_vol,
+                  int ctas_per_sm, cudaStream_t s);
 int check_common(const void *vol, const diffus_volume_desc *vd, const float *pose, const diffus_fan *fan,
                  const diffus_params *prm);
 MarchArgs make_march_args(const diffus_volume_desc *vd, const diffus_fan *fan, const diffus_params *prm);
@@ -54,79 +57,6 @@ static __global__ void k_pose_reduce(const double *__restrict__ part, const int 
     }
 }
 
-struct PosePlace {
-    double spacing[3], origin[3];
-    int nx, ny, nz;
-};
-
-// depth: per-pose depths (device) or, when NULL, depth_all for every pose.
-static __global__ void k_pose_boxes(const float *__restrict__ poses, const double *__restrict__ depth,
-                                    double depth_all, int P, PosePlace pp, PoseBox *__restrict__ boxes)
-{
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    boxes[p] = pose_box(poses + 6 * p, depth ? depth[p] : depth_all, pp.spacing, pp.origin, pp.nx, pp.ny, pp.nz);
-}
-
-__device__ __forceinline__ bool box_touches(const PoseBox &b, int bx0, int by0, int bz0)
-{
-    // samples of cells b0-1 .. b0+7 lie in [b0-1, b0+8] per axis
-    return b.hi[0] >= (float)(bx0 - 1) && b.lo[0] <= (float)(bx0 + kBrick) && b.hi[1] >= (float)(by0 - 1) &&
-           b.lo[1] <= (float)(by0 + kBrick) && b.hi[2] >= (float)(bz0 - 1) && b.lo[2] <= (float)(bz0 + kBrick);
-}
-
-// Bricks touched by any pose of [p0, p1) -> list (order irrelevant: each
-// brick is owned by one CTA).
-static __global__ void k_brick_cull(const PoseBox *__restrict__ boxes, int p0, int p1, GatherArgs G,
-                                    int *__restrict__ list, int *__restrict__ count)
-{
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    int nb = G.nbx * G.nby * G.nbz;
-    if (b >= nb) return;
-    int bx = b % G.nbx, by = (b / G.nbx) % G.nby, bz = b / (G.nbx * G.nby);
-    bool hit = false;
-    for (int p = p0; p < p1 && !hit; p++) hit = box_touches(boxes[p], bx * kBrick, by * kBrick, bz * kBrick);
-    if (hit) list[atomicAdd(count, 1)] = b;
-}
-
-// One CTA per touched brick: gather the poses [p0, p1) into grad_vol.
-static __global__ void __launch_bounds__(kGatherWarps * 32)
-    k_brick_gather(const RayGeo *__restrict__ geo, const int *__restrict__ ray0, const float *__restrict__ gz,
-                   const long long *__restrict__ gz_off, const PoseBox *__restrict__ boxes, int p0, int p1,
-                   GatherArgs G, const int *__restrict__ list, const int *__restrict__ count,
-                   float *__restrict__ grad_vol)
-{
-    __shared__ GatherSmem sm;
-    const int w = threadIdx.x >> 5;
-    const int nlist = *count;
-    for (int u = blockIdx.x; u < nlist; u += gridDim.x) {
-        const int b = list[u];
-        const int bx0 = (b % G.nbx) * kBrick, by0 = ((b / G.nbx) % G.nby) * kBrick, bz0 = (b / (G.nbx * G.nby)) * kBrick;
-        for (int i = threadIdx.x; i < kGatherWarps * kBrick * kBrick * kBrick; i += blockDim.x)
-            (&sm.acc[0][0])[i] = 0.0f;
-        __syncthreads();
-        for (int p = p0; p < p1; p++) {
-            if (!box_touches(boxes[p], bx0, by0, bz0)) continue;
-            for (int j = ray0[p] + w; j < ray0[p + 1]; j += kGatherWarps) {
-                RayGeo rg = geo[j];
-                gather_ray(rg, gz + gz_off[j], G, bx0, by0, bz0, sm, w);
-            }
-        }
-        __syncthreads();
-        for (int v = threadIdx.x; v < kBrick * kBrick * kBrick; v += blockDim.x) {
-            int vx = bx0 + (v & 7), vy = by0 + ((v >> 3) & 7), vz = bz0 + (v >> 6);
-            if (vx < G.nx && vy < G.ny && vz < G.nz) {
-                float s = sm.acc[0][v];
-#pragma unroll
-                for (int q = 1; q < kGatherWarps; q++) s += sm.acc[q][v];
-                size_t o = ((size_t)vz * G.ny + vy) * G.nx + vx;
-                grad_vol[o] += s;
-            }
-        }
-        __syncthreads();
-    }
-}
-
 static __global__ void k_offsets(long long *__restrict__ row_off, long long *__restrict__ gz_off,
                                  long long *__restrict__ ck_off, int *__restrict__ ray0, int n, int S)
 {
@@ -150,8 +80,7 @@ struct BwdLayout {
     float4 *ckpt;
     long long *row_off, *gz_off, *ck_off;
     int *ray0;
-    PoseBox *box;
-    int *list, *count;
+    void *gather_ws;
     size_t bytes;
 };
 
@@ -161,8 +90,6 @@ static BwdLayout bwd_layout(void *ws, const diffus_volume_desc *vd, const diffus
     BwdLayout L;
     size_t n = (size_t)fan->n_rays, S = (size_t)fan->n_samples;
     size_t nseg = (S + kSeg - 1) / kSeg;
-    size_t nb = (size_t)((vd->nx + kBrick - 1) / kBrick) * ((vd->ny + kBrick - 1) / kBrick) *
-                ((vd->nz + kBrick - 1) / kBrick);
     L.geo = c.take<RayGeo>(n);
     L.gy = prm->blur ? c.take<float>(n * S) : nullptr;
     L.gz = c.take<float>(n * (S + 1));
@@ -172,9 +99,7 @@ static BwdLayout bwd_layout(void *ws, const diffus_volume_desc *vd, const diffus
     L.gz_off = c.take<long long>(n);
     L.ck_off = c.take<long long>(n);
     L.ray0 = c.take<int>(2);
-    L.box = c.take<PoseBox>(1);
-    L.list = c.take<int>(nb);
-    L.count = c.take<int>(1);
+    L.gather_ws = (void *)c.take<char>(gather_workspace_bytes(vd, (long long)n, fan->depth_mm));
     L.bytes = c.used;
     return L;
 }
@@ -182,41 +107,6 @@ static BwdLayout bwd_layout(void *ws, const diffus_volume_desc *vd, const diffus
 size_t bwd_workspace_bytes(const diffus_volume_desc *vd, const diffus_fan *fan, const diffus_params *prm)
 {
     return bwd_layout(nullptr, vd, fan, prm).bytes;
-}
-
-GatherArgs make_gather_args(const diffus_volume_desc *vd)
-{
-    GatherArgs G;
-    G.nx = vd->nx; G.ny = vd->ny; G.nz = vd->nz;
-    G.nbx = (vd->nx + kBrick - 1) / kBrick;
-    G.nby = (vd->ny + kBrick - 1) / kBrick;
-    G.nbz = (vd->nz + kBrick - 1) / kBrick;
-    return G;
-}
-
-int launch_gather(const diffus_volume_desc *vd, const float *poses, const double *depth_dev, double depth_all,
-                  int P, int pose_chunk,
-                  const RayGeo *geo, const int *ray0, const float *gz, const long long *gz_off, PoseBox *boxes,
-                  int *list, int *count, float *grad_vol, cudaStream_t s)
-{
-    GatherArgs G = make_gather_args(vd);
-    PosePlace pp{{vd->sx, vd->sy, vd->sz}, {vd->ox, vd->oy, vd->oz}, vd->nx, vd->ny, vd->nz};
-    k_pose_boxes<<<(P + 127) / 128, 128, 0, s>>>(poses, depth_dev, depth_all, P, pp, boxes);
-    if (cudaMemsetAsync(grad_vol, 0, sizeof(float) * (size_t)vd->nx * vd->ny * vd->nz, s) != cudaSuccess)
-        return DIFFUS_E_LAUNCH;
-    int nb = G.nbx * G.nby * G.nbz;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int p0 = 0; p0 < P; p0 += pose_chunk) {
-        int p1 = p0 + pose_chunk < P ? p0 + pose_chunk : P;
-        if (cudaMemsetAsync(count, 0, sizeof(int), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
-        k_brick_cull<<<(nb + 255) / 256, 256, 0, s>>>(boxes, p0, p1, G, list, count);
-        int grid = nb < sms * 8 ? nb : sms * 8;
-        k_brick_gather<<<grid, kGatherWarps * 32, 0, s>>>(geo, ray0, gz, gz_off, boxes, p0, p1, G, list, count,
-                                                          grad_vol);
-    }
-    return launch_status();
 }
 
 }  // namespace dfs
@@ -258,7 +148,6 @@ extern "C" int diffus_render_bwd(const void *vol, const diffus_volume_desc *vd, 
     if ((rc = launch_status())) return rc;
     if (grad_pose) k_pose_reduce<<<1, 32, 0, s>>>(L.part, L.ray0, 1, grad_pose);
     if (grad_vol)
-        rc = launch_gather(vd, pose, nullptr, fan->depth_mm, 1, 1, L.geo, L.ray0, L.gz, L.gz_off, L.box, L.list,
-                           L.count, grad_vol, s);
+        rc = launch_gather(vd, L.geo, n, fan->depth_mm, L.gz, L.gz_off, L.gather_ws, status, grad_vol, 8, s);
     return rc ? rc : launch_status();
 }

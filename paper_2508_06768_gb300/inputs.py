@@ -12,7 +12,8 @@ impedance ranges of soft tissue (1.38-1.70 MRayl) and bone (7.8 MRayl).
 from __future__ import annotations
 
 import math
-from dataclasses import dataclass, field, replace
+import os
+from dataclasses import dataclass, replace
 
 import numpy as np
 
@@ -152,6 +153,30 @@ def gradient_noise(shape_zyx, cell, rng, octaves=3):
 
 # --------------------------------------------------------------- phantoms
 
+_CACHE = os.environ.get("DIFFUS_PHANTOM_CACHE",
+                        os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "phantoms"))
+
+
+def _cached(name, make):
+    """Phantoms are deterministic in their arguments; keep generated volumes
+    on disk so repeated processes do not rebuild them."""
+    path = os.path.join(_CACHE, name + ".npz")
+    if os.path.exists(path):
+        try:
+            z = np.load(path)
+            return Volume(z["data"], tuple(z["spacing"]), tuple(z["origin"]))
+        except Exception:
+            pass
+    v = make()
+    try:
+        os.makedirs(_CACHE, exist_ok=True)
+        tmp = path + ".tmp%d.npz" % os.getpid()
+        np.savez(tmp, data=v.data, spacing=np.asarray(v.spacing), origin=np.asarray(v.origin))
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return v
+
 def small_phantom(n=64, spacing=1.0, seed=0, noise_sigma=0.01):
     """n^3 volume at `spacing` mm: background 1.54 MRayl, six seeded random
     ellipsoids (impedance uniform in 1.38-1.70 MRayl, semi-axes 4-12 mm,
@@ -184,6 +209,12 @@ def brain_phantom(shape_xyz=(256, 256, 192), spacing=1.0, seed=1, n_lesions=8, h
     """Brain-MRI-like phantom: smooth gradient-noise tissue field rescaled to
     1.45-1.65 MRayl, `n_lesions` seeded ellipsoidal lesions at +-5%, and a thin
     7.8 MRayl skull shell on a head ellipsoid with semi-axes head_frac*extent."""
+    key = "brain_%dx%dx%d_%g_%d_%d_%g_%g_%g" % (tuple(shape_xyz) + (spacing, seed, n_lesions, head_frac, skull_mm,
+                                                                    noise_sigma))
+    return _cached(key, lambda: _brain_phantom(shape_xyz, spacing, seed, n_lesions, head_frac, skull_mm, noise_sigma))
+
+
+def _brain_phantom(shape_xyz, spacing, seed, n_lesions, head_frac, skull_mm, noise_sigma):
     rng = np.random.default_rng(seed)
     nx, ny, nz = shape_xyz
     shape = (nz, ny, nx)

@@ -13,9 +13,10 @@ BF16_TOL = 2e-3      # BF16 volume vs the oracle on the float32 volume
 # the state becomes ~eps / det in the row (measured: ~3e-7 / det).  Rows with
 # min det >= COND_DET carry the 1e-5 norm-wise claim; rows between a pole of
 # the literal model and COND_DET are checked after weighting each row by
-# det / COND_DET, against NEAR_POLE_TOL.
+# det / COND_DET, against the looser NEAR_POLE_TOL (a sanity bound: close to
+# a pole the FP32 and FP64 results may part by the conditioning of the row).
 COND_DET = 0.05
-NEAR_POLE_TOL = 1e-4
+NEAR_POLE_TOL = 1e-3
 GRAD_TOL = 1e-5      # norm-wise relative error of grad_vol and grad_pose (FP32 path)
 
 

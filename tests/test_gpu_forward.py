@@ -73,8 +73,20 @@ def test_bf16_volume():
     rounded = I.Volume(bf16_round(vol.data), vol.spacing, vol.origin)
     # against the oracle on the bf16-rounded volume: FP32 arithmetic error only
     _check(vol, pose, fan, prm, tol=FP32_TOL, bf16=True, oracle_vol=rounded)
-    # against the oracle on the float32 volume: quantisation of the volume
-    _check(vol, pose, fan, prm, tol=BF16_TOL, bf16=True, same_input=False)
+    # against the oracle on the float32 volume: the error is the quantisation
+    # of the volume itself (bf16 keeps 8 significant bits, a step of ~6e-3
+    # MRayl at 1.5 MRayl, the size of the tissue texture), measured here as
+    # the FP64 oracle on the rounded volume against the FP64 oracle on the
+    # original one; the CUDA path may add only FP32 rounding to it.
+    ref32, first32, det32 = oracle_render(vol, pose, fan, prm)
+    ref16, first16, _ = oracle_render(rounded, pose, fan, prm)
+    first = np.minimum(first32, first16)
+    quant, _, _, good = check_rows(ref16, ref32, first, det32, fan.n_samples, oracle.blur_halfwidth(prm), True,
+                                   FP32_TOL)
+    img, valid, _ = gpu_render(vol, pose, fan, prm, bf16=True)
+    err = np.linalg.norm((img - ref32)[good]) / np.linalg.norm(ref32[good])
+    assert err <= quant * 1.01 + FP32_TOL, (err, quant)
+    print("bf16 volume: quantisation error %.3e, CUDA path error %.3e" % (quant, err))
 
 
 def test_brain_slice_sampled_rays():
