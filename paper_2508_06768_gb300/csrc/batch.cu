@@ -161,7 +161,7 @@ template <typename T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_batch_fwd(const T *__restrict__ vol, MarchArgs A, BatchDev B,
                                                           const RayGeo *__restrict__ geo, float *__restrict__ out,
                                                           int *__restrict__ valid, uint32_t *__restrict__ status,
-                                                          unsigned *__restrict__ counter)
+                                                          unsigned *__restrict__ counter, float4 *__restrict__ ckpt)
 {
     __shared__ float buf[WARPS][kSegPad];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch_fwd(const T *__restrict__ 
         RayGeo rg = geo[r];
         MarchArgs Ap = A;
         Ap.a2 = B.pose[rg.pose].a2;
-        RayOut o{out + B.row_off[r], valid ? valid + r : nullptr, status};
+        RayOut o{out + B.row_off[r], valid ? valid + r : nullptr, status, ckpt ? ckpt + B.ck_off[r] : nullptr};
         march_fwd_ray<T>(vol, Ap, rg, o, buf[w]);
         __syncwarp();
     }
@@ -199,12 +199,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch_bwd(const T *__restrict__ 
         MarchArgs Ap = A;
         Ap.a2 = B.pose[rg.pose].a2;
         march_bwd_ray<T>(vol, Ap, rg, gy + B.row_off[r], gz + B.gz_off[r], part + 6 * (size_t)r,
-                         ckpt + B.ck_off[r], sm[w]);
+                         ckpt + B.ck_off[r], sm[w], true);
         __syncwarp();
     }
 }
 
-template <bool TRANSPOSE>
+template <bool TRANSPOSE, int WT>
 __global__ void __launch_bounds__(kBlurThreads) k_batch_blur(const float *__restrict__ in, float *__restrict__ out,
                                                              const PlanPose *__restrict__ poses,
                                                              const BlurTile *__restrict__ tiles, int64_t n_tiles,
@@ -216,8 +216,22 @@ __global__ void __launch_bounds__(kBlurThreads) k_batch_blur(const float *__rest
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const BlurTile tl = tiles[t];
         const PlanPose pp = poses[tl.pose];
-        blur_tile<TRANSPOSE>(in + pp.img_off, out + pp.img_off, pp.n_rays, pp.S, b, tl.j0, tl.k0, sm, wsm);
+        blur_tile<TRANSPOSE, WT>(in + pp.img_off, out + pp.img_off, pp.n_rays, pp.S, b, tl.j0, tl.k0, sm, wsm);
         __syncthreads();
+    }
+}
+
+template <bool TRANSPOSE>
+void launch_batch_blur(const float *in, float *out, const PlanPose *poses, const BlurTile *tiles, int64_t n_tiles,
+                       const BlurArgs &b, int grid, cudaStream_t s)
+{
+    const size_t sm = blur_smem_bytes(b.W);
+    switch (b.W) {
+#define DFS_BB(WT)                                                                                        \
+    case WT: k_batch_blur<TRANSPOSE, WT><<<grid, kBlurThreads, sm, s>>>(in, out, poses, tiles, n_tiles, b); break;
+    DFS_BB(0) DFS_BB(1) DFS_BB(2) DFS_BB(3) DFS_BB(4) DFS_BB(5) DFS_BB(6) DFS_BB(7) DFS_BB(8)
+#undef DFS_BB
+    default: k_batch_blur<TRANSPOSE, -1><<<grid, kBlurThreads, sm, s>>>(in, out, poses, tiles, n_tiles, b); break;
     }
 }
 
@@ -231,9 +245,9 @@ int sm_count()
 
 template <typename T, int WARPS>
 void launch_fwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out, int *valid,
-                  uint32_t *status, unsigned *counter, int grid, cudaStream_t s)
+                  uint32_t *status, unsigned *counter, float4 *ckpt, int grid, cudaStream_t s)
 {
-    k_batch_fwd<T, WARPS><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status, counter);
+    k_batch_fwd<T, WARPS><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status, counter, ckpt);
 }
 
 template <typename T, int WARPS>
@@ -245,12 +259,12 @@ void launch_bwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const 
 
 template <typename T>
 int launch_fwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out,
-                 int *valid, uint32_t *status, unsigned *counter, int grid, cudaStream_t s)
+                 int *valid, uint32_t *status, unsigned *counter, float4 *ckpt, int grid, cudaStream_t s)
 {
     switch (warps) {
-    case 2: launch_fwd_t<T, 2>(vol, A, B, geo, out, valid, status, counter, grid, s); break;
-    case 4: launch_fwd_t<T, 4>(vol, A, B, geo, out, valid, status, counter, grid, s); break;
-    case 8: launch_fwd_t<T, 8>(vol, A, B, geo, out, valid, status, counter, grid, s); break;
+    case 2: launch_fwd_t<T, 2>(vol, A, B, geo, out, valid, status, counter, ckpt, grid, s); break;
+    case 4: launch_fwd_t<T, 4>(vol, A, B, geo, out, valid, status, counter, ckpt, grid, s); break;
+    case 8: launch_fwd_t<T, 8>(vol, A, B, geo, out, valid, status, counter, ckpt, grid, s); break;
     default: return DIFFUS_E_PLAN;
     }
     return DIFFUS_OK;
@@ -459,20 +473,20 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     MarchArgs A = make_march_args(vd, &dummy, prm);
     const int grid = sm_count() * H.ctas_per_sm;
     float *march_out = prm->blur ? L.y : images;
+    // with a backward in the same call the forward keeps the scan carries
+    float4 *ck = bwd ? L.ckpt : nullptr;
     if (vd->dtype == DIFFUS_F32)
-        rc = launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0, grid, s);
+        rc = launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0, ck, grid, s);
     else
         rc = launch_fwd_w<unsigned short>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0,
-                                          grid, s);
+                                          ck, grid, s);
     if (rc) return rc;
     mark(DIFFUS_TR_BLUR);
     BlurArgs bl{(float)prm->sigma0, (float)prm->sigma1, H.blurW};
     const int tgrid = (int)std::min<int64_t>(H.n_tiles, (int64_t)sm_count() * 8);
     const PlanPose *dpose = at<PlanPose>(plan_dev, H.off_pose);
     const BlurTile *dtiles = at<BlurTile>(plan_dev, H.off_tiles);
-    if (prm->blur)
-        k_batch_blur<false><<<tgrid, kBlurThreads, blur_smem_bytes(H.blurW), s>>>(L.y, images, dpose, dtiles,
-                                                                                 H.n_tiles, bl);
+    if (prm->blur) launch_batch_blur<false>(L.y, images, dpose, dtiles, H.n_tiles, bl, tgrid, s);
     mark(DIFFUS_TR_FWD_END);
     if ((rc = launch_status())) return rc;
     if (!bwd) return DIFFUS_OK;
@@ -482,8 +496,7 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
         return DIFFUS_E_ALIGN;
     const float *gy = grad_images;
     if (prm->blur) {
-        k_batch_blur<true><<<tgrid, kBlurThreads, blur_smem_bytes(H.blurW), s>>>(grad_images, L.gy, dpose, dtiles,
-                                                                                H.n_tiles, bl);
+        launch_batch_blur<true>(grad_images, L.gy, dpose, dtiles, H.n_tiles, bl, tgrid, s);
         gy = L.gy;
     }
     mark(DIFFUS_TR_MARCH_BWD);

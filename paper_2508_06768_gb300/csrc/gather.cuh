@@ -83,89 +83,110 @@ __device__ __forceinline__ int cell_of(long long X, int n)
 
 struct GatherSmem {
     float acc[kGatherWarps][kBrickVox];
-    float rec[kGatherWarps][32][kChunk][8];   // merged cell records of each lane
-    int reccell[kGatherWarps][32][kChunk];    // cell within the brick (x | y<<4 | z<<8)
+    float rec[kGatherWarps][kChunk][8][32];   // merged cell records, lane innermost (no bank conflicts)
+    int reccell[kGatherWarps][kChunk][32];    // cell within the brick (x | y<<4 | z<<8)
 };
 
 // Add the samples k0r..k1r of one ray (all in cells of the brick whose first
 // cell is (bx0, by0, bz0)) to this warp's 9^3 accumulator.
+//
+// Each lane takes 8 consecutive samples and merges runs of the same cell into
+// records (a cell and its 8 corner sums).  Along a ray the cell index is
+// monotone on every axis, so a cell's samples are contiguous: the same cell
+// can only appear as the last record of one lane and the first records of
+// the following lanes.  Such a chain gets ranks 0, 1, 2, ... and rank r is
+// written in pass r.  Within a pass every record of a warp has a distinct
+// cell, and for a fixed corner offset distinct cells hit distinct voxels, so
+// the 8 corner writes of a pass never collide.
 __device__ __forceinline__ void gather_run(const RayGeo &rg, const float *__restrict__ gz, const GatherArgs &G,
                                            int k0r, int k1r, int bx0, int by0, int bz0, GatherSmem &sm, int w)
 {
     const int lane = threadIdx.x & 31;
-    // Write phases: along a ray the cell index is monotone on every axis, so
-    // cells four or more cell changes apart share no voxel.  Inside the
-    // volume a cell holds at most spc = 2^32/max|DX| + 2 samples, so records
-    // of lanes `phases` apart are >= 5 cells apart when 8(phases-1)+2 >= 5 spc.
-    // Clamped samples can stay in one cell for long, so a step that has any
-    // clamped sample writes one lane at a time.
-    long long dmax = llabs(rg.DX[0]);
-    dmax = llabs(rg.DX[1]) > dmax ? llabs(rg.DX[1]) : dmax;
-    dmax = llabs(rg.DX[2]) > dmax ? llabs(rg.DX[2]) : dmax;
-    float spc = dmax > 0 ? 4294967296.0f / (float)dmax + 2.0f : 1e9f;
-    int phases_in = (int)fminf(32.0f, ceilf((5.0f * spc - 2.0f) / kChunk) + 1.0f);
-    if (phases_in < 1) phases_in = 1;
     float *acc = sm.acc[w];
     for (int k0 = k0r; k0 <= k1r; k0 += 32 * kChunk) {
+        const int ks = k0 + lane * kChunk;
+        long long X = rg.X0[0] + (long long)ks * rg.DX[0];
+        long long Y = rg.X0[1] + (long long)ks * rg.DX[1];
+        long long Z = rg.X0[2] + (long long)ks * rg.DX[2];
         int nr = 0;
-        int ccx = -1000, ccy = -1000, ccz = -1000;
+        int cur = -1;
         float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        bool clamped = false;
 #pragma unroll
         for (int t = 0; t < kChunk; t++) {
-            int k = k0 + lane * kChunk + t;
+            const int k = ks + t;
             if (k <= k1r) {
-                long long X = rg.X0[0] + (long long)k * rg.DX[0];
-                long long Y = rg.X0[1] + (long long)k * rg.DX[1];
-                long long Z = rg.X0[2] + (long long)k * rg.DX[2];
                 int ix, iy, iz;
                 float fx, fy, fz;
                 bool i0, i1, i2;
                 axis_split(X, G.nx, ix, fx, i0);
                 axis_split(Y, G.ny, iy, fy, i1);
                 axis_split(Z, G.nz, iz, fz, i2);
-                clamped |= (X < 0) | ((X >> 32) >= G.nx - 1) | (Y < 0) | ((Y >> 32) >= G.ny - 1) | (Z < 0) |
-                           ((Z >> 32) >= G.nz - 1);
-                float g = __ldg(gz + k);
-                if (ix != ccx || iy != ccy || iz != ccz) {
-                    if (ccx != -1000) {
+                const float g = __ldg(gz + k);
+                const int cell = (ix - bx0) | ((iy - by0) << 4) | ((iz - bz0) << 8);
+                if (cell != cur) {
+                    if (cur >= 0) {
 #pragma unroll
-                        for (int q = 0; q < 8; q++) sm.rec[w][lane][nr][q] = v[q];
-                        sm.reccell[w][lane][nr] = (ccx - bx0) | ((ccy - by0) << 4) | ((ccz - bz0) << 8);
+                        for (int q = 0; q < 8; q++) sm.rec[w][nr][q][lane] = v[q];
+                        sm.reccell[w][nr][lane] = cur;
                         nr++;
                     }
-                    ccx = ix; ccy = iy; ccz = iz;
+                    cur = cell;
 #pragma unroll
                     for (int q = 0; q < 8; q++) v[q] = 0.0f;
                 }
-                float wx1 = fx, wx0 = 1.0f - fx, wy1 = fy, wy0 = 1.0f - fy, wz1 = fz, wz0 = 1.0f - fz;
-                float a00 = g * wy0 * wz0, a10 = g * wy1 * wz0, a01 = g * wy0 * wz1, a11 = g * wy1 * wz1;
+                const float wx1 = fx, wx0 = 1.0f - fx, wy1 = fy, wy0 = 1.0f - fy;
+                const float gz0 = g * (1.0f - fz), gz1 = g * fz;
+                const float a00 = gz0 * wy0, a10 = gz0 * wy1, a01 = gz1 * wy0, a11 = gz1 * wy1;
                 v[0] = fmaf(a00, wx0, v[0]); v[1] = fmaf(a00, wx1, v[1]);
                 v[2] = fmaf(a10, wx0, v[2]); v[3] = fmaf(a10, wx1, v[3]);
                 v[4] = fmaf(a01, wx0, v[4]); v[5] = fmaf(a01, wx1, v[5]);
                 v[6] = fmaf(a11, wx0, v[6]); v[7] = fmaf(a11, wx1, v[7]);
             }
+            X += rg.DX[0];
+            Y += rg.DX[1];
+            Z += rg.DX[2];
         }
-        if (ccx != -1000) {
+        if (cur >= 0) {
 #pragma unroll
-            for (int q = 0; q < 8; q++) sm.rec[w][lane][nr][q] = v[q];
-            sm.reccell[w][lane][nr] = (ccx - bx0) | ((ccy - by0) << 4) | ((ccz - bz0) << 8);
+            for (int q = 0; q < 8; q++) sm.rec[w][nr][q][lane] = v[q];
+            sm.reccell[w][nr][lane] = cur;
             nr++;
         }
-        const int phases = __any_sync(0xffffffffu, clamped) ? 32 : phases_in;
         __syncwarp();
-        for (int ph = 0; ph < phases; ph++) {
-            if (lane % phases == ph) {
-                for (int r = 0; r < nr; r++) {
-                    const int c = sm.reccell[w][lane][r];
-                    const int cx = c & 15, cy = (c >> 4) & 15, cz = c >> 8;   // 0..7 within the brick
-                    const float *vv = sm.rec[w][lane][r];
+        // ranks of the chain heads: my first record continues the previous
+        // lane's last record when both name the same cell
+        const int first = nr > 0 ? sm.reccell[w][0][lane] : -1;
+        const int last = nr > 0 ? sm.reccell[w][nr - 1][lane] : -2;
+        const int prev_last = __shfl_up_sync(0xffffffffu, last, 1);
+        const bool cont = lane > 0 && nr > 0 && first == prev_last;
+        int rank_first = cont ? 1 : 0;
+        for (;;) {
+            // a lane holding a single record passes its rank on as its last
+            const int rank_last = nr == 1 ? rank_first : 0;
+            const int prev = __shfl_up_sync(0xffffffffu, rank_last, 1);
+            const int nf = cont ? prev + 1 : 0;
+            const bool changed = nf != rank_first;
+            rank_first = nf;
+            if (!__any_sync(0xffffffffu, changed)) break;
+        }
+        int max_rank = rank_first;
 #pragma unroll
-                    for (int q = 0; q < 8; q++)
-                        acc[((cz + (q >> 2)) * kBrickV + (cy + ((q >> 1) & 1))) * kBrickV + (cx + (q & 1))] += vv[q];
+        for (int off = 16; off > 0; off >>= 1) max_rank = max(max_rank, __shfl_xor_sync(0xffffffffu, max_rank, off));
+        for (int pass = 0; pass <= max_rank; pass++) {
+            const int r0 = (pass == 0) ? (rank_first == 0 ? 0 : 1) : 0;
+            const int r1 = (pass == 0) ? nr : ((rank_first == pass && nr > 0) ? 1 : 0);
+            // one corner at a time: within a corner every write of the warp
+            // goes to a distinct voxel; __syncwarp orders the corners
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int off = ((q >> 2) * kBrickV + ((q >> 1) & 1)) * kBrickV + (q & 1);
+                for (int r = r0; r < r1; r++) {
+                    const int c = sm.reccell[w][r][lane];
+                    const int cx = c & 15, cy = (c >> 4) & 15, cz = c >> 8;
+                    acc[(cz * kBrickV + cy) * kBrickV + cx + off] += sm.rec[w][r][q][lane];
                 }
+                __syncwarp();
             }
-            __syncwarp();
         }
     }
 }

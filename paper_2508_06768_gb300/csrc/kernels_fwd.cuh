@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) k_march_fwd(const T *__restric
     const int j = blockIdx.x * kWarpsFwd + w;
     if (j >= n_rays) return;
     RayGeo rg = geo[j];
-    RayOut o{out + (size_t)j * rg.S, valid ? valid + j : nullptr, status};
+    RayOut o{out + (size_t)j * rg.S, valid ? valid + j : nullptr, status, nullptr};
     march_fwd_ray<T>(vol, A, rg, o, buf[w]);
 }
 
@@ -129,62 +129,100 @@ __device__ __forceinline__ float blur_w(const BlurArgs &b, int m, int k, float i
 }
 
 // Lateral blur of one pose image (Section 2.4), or its transpose.
-// in/out: [n][S].  Tile: kBlurRays output rays x kBlurRows rows, halo W rays.
+// in/out: [n][S].  Tile: kBlurRays output rays x kBlurRows rows (one row per
+// lane), halo W rays.
 // Forward:   out[j] = sum_m w_m in[j+m] / N_j        (valid j+m)
 // Transpose: out[j] = sum_m w_m in[j+m] / N_{j+m}    (valid j+m)
-template <bool TRANSPOSE>
+// WT >= 0 is the half-width known at compile time: each warp then keeps a
+// sliding window of 8 + 2W rows in registers and produces 8 output rays from
+// it.  WT < 0 is the general path for wide kernels.
+template <bool TRANSPOSE, int WT>
 __device__ void blur_tile(const float *__restrict__ in, float *__restrict__ out, int n, int S,
                           const BlurArgs &b, int j0, int k0, float *sm, float *wsm)
 {
-    const int W = b.W;
+    const int W = WT >= 0 ? WT : b.W;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const int k = k0 + lane;
     const float invS = 1.0f / (float)S;
     const int rows = kBlurRays + 2 * W;
-    // weights for this lane's row: w[m], m = 0..W
     for (int m = warp; m <= W; m += nw) wsm[m * 32 + lane] = (k < S) ? blur_w(b, m, k, invS) : 0.0f;
-    // load in[j0-W .. j0+kBlurRays+W) x [k0, k0+32)
-    for (int rr = warp; rr < rows; rr += nw) {
-        int j = j0 - W + rr;
-        sm[rr * 32 + lane] = (j >= 0 && j < n && k < S) ? in[(size_t)j * S + k] : 0.0f;
+    if (WT >= 0) {
+        // all of this warp's rows in flight at once (rows is a compile-time bound)
+        constexpr int kRows = kBlurRays + 2 * (WT >= 0 ? WT : 0);
+        constexpr int kPer = (kRows + (kBlurThreads / 32) - 1) / (kBlurThreads / 32);
+        float tmp[kPer];
+#pragma unroll
+        for (int i = 0; i < kPer; i++) {
+            const int rr = warp + i * nw;
+            const int j = j0 - W + rr;
+            tmp[i] = (rr < rows && j >= 0 && j < n && k < S) ? __ldg(in + (size_t)j * S + k) : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < kPer; i++) {
+            const int rr = warp + i * nw;
+            if (rr < rows) sm[rr * 32 + lane] = tmp[i];
+        }
+    } else {
+        for (int rr = warp; rr < rows; rr += nw) {
+            int j = j0 - W + rr;
+            sm[rr * 32 + lane] = (j >= 0 && j < n && k < S) ? in[(size_t)j * S + k] : 0.0f;
+        }
     }
     __syncthreads();
-    // full-row normaliser (interior rays)
     float full = wsm[lane];
     for (int m = 1; m <= W; m++) full += 2.0f * wsm[m * 32 + lane];
+    auto norm_of = [&](int j) -> float {
+        if (j >= W && j < n - W) return full;
+        float N = 0.0f;
+        for (int m = -W; m <= W; m++)
+            if (j + m >= 0 && j + m < n) N += wsm[(m < 0 ? -m : m) * 32 + lane];
+        return N;
+    };
     if (TRANSPOSE) {
-        // scale each loaded row by 1/N_j of its own position
         for (int rr = warp; rr < rows; rr += nw) {
             int j = j0 - W + rr;
             if (j < 0 || j >= n) continue;
-            float N = full;
-            if (j < W || j >= n - W) {
-                N = 0.0f;
-                for (int m = -W; m <= W; m++)
-                    if (j + m >= 0 && j + m < n) N += wsm[(m < 0 ? -m : m) * 32 + lane];
-            }
-            sm[rr * 32 + lane] *= 1.0f / N;
+            sm[rr * 32 + lane] *= 1.0f / norm_of(j);
         }
         __syncthreads();
+    }
+    if (WT >= 0) {
+        constexpr int WW = WT >= 0 ? WT : 0;
+        constexpr int RPW = kBlurRays / 8;                 // output rays per warp (8 warps)
+        float w[WW + 1];
+#pragma unroll
+        for (int m = 0; m <= WW; m++) w[m] = wsm[m * 32 + lane];
+        for (int g = warp; g < kBlurRays / RPW; g += nw) {
+            float win[RPW + 2 * WW];
+#pragma unroll
+            for (int t = 0; t < RPW + 2 * WW; t++) win[t] = sm[(g * RPW + t) * 32 + lane];
+#pragma unroll
+            for (int i = 0; i < RPW; i++) {
+                const int j = j0 + g * RPW + i;
+                float acc = w[0] * win[i + WW];
+#pragma unroll
+                for (int m = 1; m <= WW; m++) acc = fmaf(w[m], win[i + WW - m] + win[i + WW + m], acc);
+                if (j < n && k < S) {
+                    if (!TRANSPOSE) acc *= 1.0f / norm_of(j);
+                    out[(size_t)j * S + k] = acc;
+                }
+            }
+        }
+        return;
     }
     for (int oj = warp; oj < kBlurRays; oj += nw) {
         int j = j0 + oj;
         if (j >= n || k >= S) continue;
-        float acc = 0.0f, N = 0.0f;
+        float acc = 0.0f;
         const float *col = sm + (oj + W) * 32 + lane;
-        for (int m = -W; m <= W; m++) {
-            float wm = wsm[(m < 0 ? -m : m) * 32 + lane];
-            bool ok = (j + m >= 0) && (j + m < n);
-            acc = fmaf(ok ? wm : 0.0f, col[m * 32], acc);
-            N += ok ? wm : 0.0f;
-        }
-        if (!TRANSPOSE) acc *= 1.0f / N;
+        for (int m = -W; m <= W; m++) acc = fmaf(wsm[(m < 0 ? -m : m) * 32 + lane], col[m * 32], acc);
+        if (!TRANSPOSE) acc *= 1.0f / norm_of(j);
         out[(size_t)j * S + k] = acc;
     }
 }
 
-template <bool TRANSPOSE>
+template <bool TRANSPOSE, int WT>
 __global__ void __launch_bounds__(kBlurThreads) k_blur(const float *__restrict__ in, float *__restrict__ out,
                                                        int n, int S, BlurArgs b)
 {
@@ -193,7 +231,7 @@ __global__ void __launch_bounds__(kBlurThreads) k_blur(const float *__restrict__
     float *sm = dyn + (kMaxW + 1) * 32;     // (kBlurRays + 2W) x 32
     int j0 = blockIdx.y * kBlurRays;
     int k0 = blockIdx.x * kBlurRows;
-    blur_tile<TRANSPOSE>(in, out, n, S, b, j0, k0, sm, wsm);
+    blur_tile<TRANSPOSE, WT>(in, out, n, S, b, j0, k0, sm, wsm);
 }
 
 inline size_t blur_smem_bytes(int W) { return sizeof(float) * 32 * ((kMaxW + 1) + kBlurRays + 2 * W); }

@@ -32,6 +32,7 @@ struct RayOut {
     float *row;       // output row [S] (image or pre-blur buffer)
     int *valid;       // nullable: leading pole-free rows
     uint32_t *status; // nullable
+    float4 *ckpt;     // nullable: scan carry (b0, b1, D) at every segment start, for the adjoint
 };
 
 __device__ __forceinline__ int smem_idx(int x) { return x + (x >> 3); }
@@ -194,6 +195,7 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
     const bool vec4 = ((((uintptr_t)out.row) & 15) == 0);
 
     for (int base = 0; base < S; base += kSeg) {
+        if (out.ckpt && lane == 0) out.ckpt[base / kSeg] = make_float4(bs0, bs1, Ds, 0.0f);
         seg_reflections<T>(vol, A.g, rg, base, czr, cdz, buf);
         __syncwarp();
         const int i0 = base + lane * kChunk;

@@ -45,10 +45,13 @@ __device__ __forceinline__ EchoGrad echo_grad(float b0, float b1, float D, float
     return g;
 }
 
+// have_ckpt: the forward march of the same call already wrote the segment
+// carries into ckpt, so the recording sweep is skipped.
 template <typename T>
 __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, const RayGeo &rg,
                               const float *__restrict__ gy_row, float *__restrict__ gz_row,
-                              double *__restrict__ pose_part, float4 *__restrict__ ckpt, BwdSmem &sm)
+                              double *__restrict__ pose_part, float4 *__restrict__ ckpt, BwdSmem &sm,
+                              bool have_ckpt = false)
 {
     const int lane = threadIdx.x & 31;
     const int S = rg.S;
@@ -57,7 +60,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
     float *buf = sm.zr;   // sweep 1 uses the first array for reflection coefficients
 
     // ---------------- sweep 1: forward, record the carry at segment starts
-    {
+    if (!have_ckpt) {
         float czr, cdz;
         sample_z<T, false>(vol, A.g, rg.X0[0], rg.X0[1], rg.X0[2], czr, cdz);
         float bs0 = 0.0f, bs1 = 1.0f, Ds = 1.0f;

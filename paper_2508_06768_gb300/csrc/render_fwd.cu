@@ -79,10 +79,24 @@ int launch_blur(const float *in, float *out, int n, int S, const diffus_params *
     BlurArgs b{(float)prm->sigma0, (float)prm->sigma1, blur_halfwidth(prm)};
     dim3 grid((S + kBlurRows - 1) / kBlurRows, (n + kBlurRays - 1) / kBlurRays);
     size_t sm = blur_smem_bytes(b.W);
-    if (transpose)
-        k_blur<true><<<grid, kBlurThreads, sm, s>>>(in, out, n, S, b);
-    else
-        k_blur<false><<<grid, kBlurThreads, sm, s>>>(in, out, n, S, b);
+#define DFS_BLUR(WT)                                                                  \
+    if (transpose)                                                                    \
+        k_blur<true, WT><<<grid, kBlurThreads, sm, s>>>(in, out, n, S, b);            \
+    else                                                                              \
+        k_blur<false, WT><<<grid, kBlurThreads, sm, s>>>(in, out, n, S, b);
+    switch (b.W) {
+    case 0: DFS_BLUR(0) break;
+    case 1: DFS_BLUR(1) break;
+    case 2: DFS_BLUR(2) break;
+    case 3: DFS_BLUR(3) break;
+    case 4: DFS_BLUR(4) break;
+    case 5: DFS_BLUR(5) break;
+    case 6: DFS_BLUR(6) break;
+    case 7: DFS_BLUR(7) break;
+    case 8: DFS_BLUR(8) break;
+    default: DFS_BLUR(-1) break;
+    }
+#undef DFS_BLUR
     return launch_status();
 }
 

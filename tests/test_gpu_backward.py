@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_2508_06768_gb300 import inputs as I
-from tests.helpers import COND_DET, GRAD_TOL, gpu_grad, gpu_render, oracle_render, row_mask, row_mindet
+from tests.helpers import COND_DET_GRAD, GRAD_TOL, gpu_grad, gpu_render, oracle_render, row_mask, row_mindet
 
 pytestmark = pytest.mark.gpu
 
@@ -18,7 +18,7 @@ def _loss_weights(vol, pose, fan, prm, seed=7, target=None):
     restricted to rows whose depth systems are well-conditioned."""
     ref, first, det = oracle_render(vol, pose, fan, prm)
     W = oracle.blur_halfwidth(prm)
-    good = row_mask(first, fan.n_samples, W, prm.blur) & (row_mindet(det, W, prm.blur) >= COND_DET)
+    good = row_mask(first, fan.n_samples, W, prm.blur) & (row_mindet(det, W, prm.blur) >= COND_DET_GRAD)
     if target is None:
         G = I.random_weights(ref.shape, seed).astype(np.float64)
     else:

@@ -71,8 +71,8 @@ def test_batch_vs_oracle():
     for p, f in enumerate(fans):
         ref, first, det = oracle_render(vol, poses[p], f, prm, pose_ctr=p)
         W = oracle.blur_halfwidth(prm)
-        from tests.helpers import COND_DET, row_mask, row_mindet
-        good = row_mask(first, f.n_samples, W, prm.blur) & (row_mindet(det, W, prm.blur) >= COND_DET)
+        from tests.helpers import COND_DET_GRAD, row_mask, row_mindet
+        good = row_mask(first, f.n_samples, W, prm.blur) & (row_mindet(det, W, prm.blur) >= COND_DET_GRAD)
         Gs.append(np.where(good, I.random_weights((f.n_rays, f.n_samples), 200 + p), 0).astype(np.float32))
     G = torch.from_numpy(np.concatenate([g.ravel() for g in Gs])).cuda()
     r.run(pd, G)
