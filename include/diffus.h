@@ -59,7 +59,8 @@ enum {
     DIFFUS_E_WORKSPACE = -6,   /* workspace missing or too small */
     DIFFUS_E_LAUNCH = -7,      /* a CUDA launch or async call failed */
     DIFFUS_E_PLAN = -8,        /* batch plan corrupt or for other inputs */
-    DIFFUS_E_DEVICE = -9       /* no usable CUDA device / wrong architecture */
+    DIFFUS_E_DEVICE = -9,      /* no usable CUDA device / wrong architecture */
+    DIFFUS_E_SCRATCH = -10     /* request larger than the static scratch of diffus_render_fwd_noalloc */
 };
 
 enum { DIFFUS_F32 = 0, DIFFUS_BF16 = 1 };
@@ -153,6 +154,28 @@ int diffus_render_bwd(const void *vol, const diffus_volume_desc *vd, const float
                       const diffus_fan *fan, const diffus_params *prm, const float *grad_image,
                       float *grad_vol, float *grad_pose, uint32_t *status, void *workspace,
                       size_t ws_bytes, diffus_stream_t stream);
+
+/* Bytes of the static device scratch of diffus_render_fwd_noalloc. */
+#define DIFFUS_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* diffus_render_fwd for callers that cannot allocate device memory while
+ * they run (for example code inside a CUDA graph capture, a real-time loop
+ * that forbids allocation, or a plug-in whose host application owns all
+ * device memory).  No workspace is passed and nothing is allocated: the
+ * scratch is a fixed file-scope device array of DIFFUS_NOALLOC_SCRATCH_BYTES
+ * (16 MiB) that every GPU loading the library holds until the process exits.
+ * A request whose forward workspace (diffus_workspace_bytes(..., 0)) exceeds
+ * it returns DIFFUS_E_SCRATCH before any launch; 16 MiB covers, for example,
+ * 256 rays x 16384 samples or 2048 rays x 2048 samples with the blur on.
+ * The first call on a device looks up the array's device address (once, with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the one array: calls whose work overlaps on the GPU
+ * (other streams, other host threads) race on it and must be serialised by
+ * the caller.  The paper has no counterpart: this is a deployment variant.
+ * Arguments and results are those of diffus_render_fwd. */
+int diffus_render_fwd_noalloc(const void *vol, const diffus_volume_desc *vd, const float *pose,
+                              const diffus_fan *fan, const diffus_params *prm, float *image,
+                              int32_t *ray_valid, uint32_t *status, diffus_stream_t stream);
 
 /* ---------------------------------------------------------------- batched */
 

@@ -86,6 +86,7 @@ def load(build_if_missing: bool = True):
         lib.diffus_strerror.restype = C.c_char_p
         lib.diffus_version.restype = C.c_int
         lib.diffus_philox.argtypes = [vp, C.c_int64, C.c_uint64, vp, vp]
+        lib.diffus_render_fwd_noalloc.argtypes = [vp, p(VolumeDesc), vp, p(FanDesc), p(ParamsDesc), vp, vp, vp, vp]
         _lib = lib
         return lib
 
@@ -172,6 +173,20 @@ def render_fwd(vol, spacing, origin, pose, fan, params, image=None, ray_valid=No
     rc = lib.diffus_render_fwd(_ptr(vol), C.byref(vd), _ptr(pose), C.byref(fd), C.byref(pd), _ptr(image),
                                _ptr(ray_valid), _ptr(status), _ptr(workspace), workspace.numel(), _stream(stream))
     _check(rc, "diffus_render_fwd")
+    return image, ray_valid, status
+
+
+def render_fwd_noalloc(vol, spacing, origin, pose, fan, params, image, ray_valid=None, status=None, stream=None,
+                       pose_ctr: int = 0):
+    """diffus_render_fwd_noalloc: the forward with the library's static
+    scratch instead of a workspace; `image` (and the optional outputs) must
+    be allocated by the caller beforehand."""
+    lib = load()
+    _require_cuda(vol, pose, image, ray_valid, status)
+    vd, fd, pd = volume_desc(vol, spacing, origin), fan_desc(fan), params_desc(params, pose_ctr)
+    rc = lib.diffus_render_fwd_noalloc(_ptr(vol), C.byref(vd), _ptr(pose), C.byref(fd), C.byref(pd), _ptr(image),
+                                       _ptr(ray_valid), _ptr(status), _stream(stream))
+    _check(rc, "diffus_render_fwd_noalloc")
     return image, ray_valid, status
 
 

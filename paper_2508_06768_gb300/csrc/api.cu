@@ -28,6 +28,7 @@ extern "C" const char *diffus_strerror(int code)
     case DIFFUS_E_LAUNCH: return "a CUDA launch or asynchronous call failed";
     case DIFFUS_E_PLAN: return "batch plan corrupt or made for other inputs";
     case DIFFUS_E_DEVICE: return "no usable CUDA device";
+    case DIFFUS_E_SCRATCH: return "request exceeds the static scratch of the no-allocation entry point";
     default: return "unknown error";
     }
 }
