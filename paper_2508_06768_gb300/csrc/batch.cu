@@ -111,6 +111,7 @@ struct BatchLayout {
     float *y;        // pre-blur rows (blur on)
     unsigned *counter;
     float *gy;       // blur transpose of grad_images (blur on)
+    float *mbuf;     // speckle factors of every row, kept by the forward for the adjoint (speckle on)
     float *gz;
     double *part;
     float4 *ckpt;
@@ -118,7 +119,7 @@ struct BatchLayout {
     size_t fwd_bytes, bytes;
 };
 
-BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc *vd, bool blur)
+BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc *vd, bool blur, bool speckle)
 {
     Carve c(ws);
     BatchLayout L;
@@ -127,6 +128,7 @@ BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc
     L.y = blur ? c.take<float>((size_t)H.total_img) : nullptr;
     L.fwd_bytes = c.used;
     L.gy = blur ? c.take<float>((size_t)H.total_img) : nullptr;
+    L.mbuf = speckle ? c.take<float>((size_t)H.total_img) : nullptr;
     L.gz = c.take<float>((size_t)H.total_gz);
     L.part = c.take<double>(6 * (size_t)H.total_rays);
     L.ckpt = c.take<float4>((size_t)H.total_ckpt);
@@ -161,7 +163,8 @@ template <typename T, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_batch_fwd(const T *__restrict__ vol, MarchArgs A, BatchDev B,
                                                           const RayGeo *__restrict__ geo, float *__restrict__ out,
                                                           int *__restrict__ valid, uint32_t *__restrict__ status,
-                                                          unsigned *__restrict__ counter, float4 *__restrict__ ckpt)
+                                                          unsigned *__restrict__ counter, float4 *__restrict__ ckpt,
+                                                          float *__restrict__ mbuf)
 {
     __shared__ float buf[WARPS][kSegPad];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -174,7 +177,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch_fwd(const T *__restrict__ 
         RayGeo rg = geo[r];
         MarchArgs Ap = A;
         Ap.a2 = B.pose[rg.pose].a2;
-        RayOut o{out + B.row_off[r], valid ? valid + r : nullptr, status, ckpt ? ckpt + B.ck_off[r] : nullptr};
+        RayOut o{out + B.row_off[r], valid ? valid + r : nullptr, status, ckpt ? ckpt + B.ck_off[r] : nullptr,
+                 mbuf ? mbuf + B.row_off[r] : nullptr};
         march_fwd_ray<T>(vol, Ap, rg, o, buf[w]);
         __syncwarp();
     }
@@ -185,7 +189,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch_bwd(const T *__restrict__ 
                                                           const RayGeo *__restrict__ geo,
                                                           const float *__restrict__ gy, float *__restrict__ gz,
                                                           double *__restrict__ part, float4 *__restrict__ ckpt,
-                                                          unsigned *__restrict__ counter)
+                                                          unsigned *__restrict__ counter,
+                                                          const float *__restrict__ mbuf)
 {
     __shared__ BwdSmem sm[WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch_bwd(const T *__restrict__ 
         MarchArgs Ap = A;
         Ap.a2 = B.pose[rg.pose].a2;
         march_bwd_ray<T>(vol, Ap, rg, gy + B.row_off[r], gz + B.gz_off[r], part + 6 * (size_t)r,
-                         ckpt + B.ck_off[r], sm[w], true);
+                         ckpt + B.ck_off[r], sm[w], true, mbuf ? mbuf + B.row_off[r] : nullptr);
         __syncwarp();
     }
 }
@@ -245,26 +250,28 @@ int sm_count()
 
 template <typename T, int WARPS>
 void launch_fwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out, int *valid,
-                  uint32_t *status, unsigned *counter, float4 *ckpt, int grid, cudaStream_t s)
+                  uint32_t *status, unsigned *counter, float4 *ckpt, float *mbuf, int grid, cudaStream_t s)
 {
-    k_batch_fwd<T, WARPS><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status, counter, ckpt);
+    k_batch_fwd<T, WARPS><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status, counter, ckpt,
+                                                      mbuf);
 }
 
 template <typename T, int WARPS>
 void launch_bwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, const float *gy,
-                  float *gz, double *part, float4 *ckpt, unsigned *counter, int grid, cudaStream_t s)
+                  float *gz, double *part, float4 *ckpt, unsigned *counter, const float *mbuf, int grid,
+                  cudaStream_t s)
 {
-    k_batch_bwd<T, WARPS><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, gy, gz, part, ckpt, counter);
+    k_batch_bwd<T, WARPS><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf);
 }
 
 template <typename T>
 int launch_fwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out,
-                 int *valid, uint32_t *status, unsigned *counter, float4 *ckpt, int grid, cudaStream_t s)
+                 int *valid, uint32_t *status, unsigned *counter, float4 *ckpt, float *mbuf, int grid, cudaStream_t s)
 {
     switch (warps) {
-    case 2: launch_fwd_t<T, 2>(vol, A, B, geo, out, valid, status, counter, ckpt, grid, s); break;
-    case 4: launch_fwd_t<T, 4>(vol, A, B, geo, out, valid, status, counter, ckpt, grid, s); break;
-    case 8: launch_fwd_t<T, 8>(vol, A, B, geo, out, valid, status, counter, ckpt, grid, s); break;
+    case 2: launch_fwd_t<T, 2>(vol, A, B, geo, out, valid, status, counter, ckpt, mbuf, grid, s); break;
+    case 4: launch_fwd_t<T, 4>(vol, A, B, geo, out, valid, status, counter, ckpt, mbuf, grid, s); break;
+    case 8: launch_fwd_t<T, 8>(vol, A, B, geo, out, valid, status, counter, ckpt, mbuf, grid, s); break;
     default: return DIFFUS_E_PLAN;
     }
     return DIFFUS_OK;
@@ -272,12 +279,12 @@ int launch_fwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev 
 
 template <typename T>
 int launch_bwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, const float *gy,
-                 float *gz, double *part, float4 *ckpt, unsigned *counter, int grid, cudaStream_t s)
+                 float *gz, double *part, float4 *ckpt, unsigned *counter, const float *mbuf, int grid, cudaStream_t s)
 {
     switch (warps) {
-    case 2: launch_bwd_t<T, 2>(vol, A, B, geo, gy, gz, part, ckpt, counter, grid, s); break;
-    case 4: launch_bwd_t<T, 4>(vol, A, B, geo, gy, gz, part, ckpt, counter, grid, s); break;
-    case 8: launch_bwd_t<T, 8>(vol, A, B, geo, gy, gz, part, ckpt, counter, grid, s); break;
+    case 2: launch_bwd_t<T, 2>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, grid, s); break;
+    case 4: launch_bwd_t<T, 4>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, grid, s); break;
+    case 8: launch_bwd_t<T, 8>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, grid, s); break;
     default: return DIFFUS_E_PLAN;
     }
     return DIFFUS_OK;
@@ -414,7 +421,7 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
                      [&](int32_t x, int32_t y) { return pp[ray_pose[x]].S > pp[ray_pose[y]].S; });
     std::copy(ord.begin(), ord.end(), order);
 
-    BatchLayout L = batch_layout(nullptr, H, vd, prm->blur != 0);
+    BatchLayout L = batch_layout(nullptr, H, vd, prm->blur != 0, prm->speckle != 0);
     if (ws_fwd) *ws_fwd = L.fwd_bytes;
     if (ws_bwd) *ws_bwd = L.bytes;
     return DIFFUS_OK;
@@ -438,7 +445,7 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
         ((uintptr_t)workspace) % 256 || ((uintptr_t)plan_dev) % 256)
         return DIFFUS_E_ALIGN;
     const bool bwd = grad_images != nullptr;
-    BatchLayout L = batch_layout(workspace, H, vd, prm->blur != 0);
+    BatchLayout L = batch_layout(workspace, H, vd, prm->blur != 0, prm->speckle != 0);
     if (ws_bytes < (bwd ? L.bytes : L.fwd_bytes)) return DIFFUS_E_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -475,11 +482,13 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     float *march_out = prm->blur ? L.y : images;
     // with a backward in the same call the forward keeps the scan carries
     float4 *ck = bwd ? L.ckpt : nullptr;
+    float *mb = bwd ? L.mbuf : nullptr;
     if (vd->dtype == DIFFUS_F32)
-        rc = launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0, ck, grid, s);
+        rc = launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0, ck, mb, grid,
+                                 s);
     else
         rc = launch_fwd_w<unsigned short>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0,
-                                          ck, grid, s);
+                                          ck, mb, grid, s);
     if (rc) return rc;
     mark(DIFFUS_TR_BLUR);
     BlurArgs bl{(float)prm->sigma0, (float)prm->sigma1, H.blurW};
@@ -501,10 +510,10 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     }
     mark(DIFFUS_TR_MARCH_BWD);
     if (vd->dtype == DIFFUS_F32)
-        rc = launch_bwd_w<float>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, grid, s);
+        rc = launch_bwd_w<float>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, L.mbuf, grid, s);
     else
-        rc = launch_bwd_w<unsigned short>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, grid,
-                                          s);
+        rc = launch_bwd_w<unsigned short>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, L.mbuf,
+                                          grid, s);
     if (rc) return rc;
     mark(DIFFUS_TR_POSE);
     const int32_t *ray0 = at<int32_t>(plan_dev, H.off_ray0);

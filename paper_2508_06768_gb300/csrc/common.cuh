@@ -118,6 +118,10 @@ __device__ __forceinline__ void sample_z(const T *__restrict__ vol, const VolGeo
     }
 }
 
+// Reciprocal on the special-function unit (<= 2 ulp): ample for the 1e-5
+// tolerance, and far cheaper than the IEEE-rounded one.
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+
 // Signed reflection coefficient r = (Z2 - Z1)/(Z1 + Z2) of Eq. 1 from two
 // samples in (zref, dz) form.
 __device__ __forceinline__ float refl(float zr1, float dz1, float zr2, float dz2)

@@ -250,11 +250,10 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
         const int bx0 = (b % G.nbx) * kBrick, by0 = ((b / G.nbx) % G.nby) * kBrick, bz0 = (b / (G.nbx * G.nby)) * kBrick;
         for (int i = threadIdx.x; i < kGatherWarps * kBrickVox; i += blockDim.x) (&sm.acc[0][0])[i] = 0.0f;
         __syncthreads();
-        for (uint32_t q = r0 + w; q < r1; q += kGatherWarps) {
-            const Run run = runs[sorted_vals[q]];
-            const RayGeo rg = geo[run.ray];
-            gather_run(rg, gz + gz_off[run.ray], G, run.k0, run.k1, bx0, by0, bz0, sm, w);
-        }
+        // warp w takes the w-th quarter of the unit's runs (in ray order)
+        const uint32_t n = r1 - r0, per = (n + kGatherWarps - 1) / kGatherWarps;
+        const uint32_t qa = r0 + min(n, per * w), qb = r0 + min(n, per * (w + 1));
+        if (qa < qb) gather_runs(runs, sorted_vals, qa, qb, geo, gz, gz_off, G, bx0, by0, bz0, sm, w);
         __syncthreads();
         float *out = upart + (size_t)u * kBrickVox;
         for (int v = threadIdx.x; v < kBrickVox; v += blockDim.x) {

@@ -81,109 +81,168 @@ __device__ __forceinline__ int cell_of(long long X, int n)
     return X < 0 ? 0 : (hi > n - 2 ? n - 2 : hi);
 }
 
+constexpr int kGSteps = 4;     // samples a lane may advance per warp step
+
 struct GatherSmem {
     float acc[kGatherWarps][kBrickVox];
-    float rec[kGatherWarps][kChunk][8][32];   // merged cell records, lane innermost (no bank conflicts)
-    int reccell[kGatherWarps][kChunk][32];    // cell within the brick (x | y<<4 | z<<8)
+    float rec[kGatherWarps][8][33];   // one record per lane (corner-major, padded)
 };
 
-// Add the samples k0r..k1r of one ray (all in cells of the brick whose first
-// cell is (bx0, by0, bz0)) to this warp's 9^3 accumulator.
-//
-// Each lane takes 8 consecutive samples and merges runs of the same cell into
-// records (a cell and its 8 corner sums).  Along a ray the cell index is
-// monotone on every axis, so a cell's samples are contiguous: the same cell
-// can only appear as the last record of one lane and the first records of
-// the following lanes.  Such a chain gets ranks 0, 1, 2, ... and rank r is
-// written in pass r.  Within a pass every record of a warp has a distinct
-// cell, and for a fixed corner offset distinct cells hit distinct voxels, so
-// the 8 corner writes of a pass never collide.
-__device__ __forceinline__ void gather_run(const RayGeo &rg, const float *__restrict__ gz, const GatherArgs &G,
-                                           int k0r, int k1r, int bx0, int by0, int bz0, GatherSmem &sm, int w)
+// Cell index and weight of one axis.  CLAMP = false is the fast path for a
+// run that never leaves the volume: identical results to axis_split there.
+template <bool CLAMP>
+__device__ __forceinline__ void gather_axis(long long X, int n, int &i0, float &f)
+{
+    if (CLAMP) {
+        bool in;
+        axis_split(X, n, i0, f, in);
+    } else {
+        i0 = (int)(X >> 32);
+        f = __uint_as_float(0x3F800000u | ((unsigned)X >> 9)) - 1.0f;
+    }
+}
+
+__device__ __forceinline__ bool inside_all(const RayGeo &rg, const GatherArgs &G, int k)
+{
+    long long X = rg.X0[0] + (long long)k * rg.DX[0];
+    long long Y = rg.X0[1] + (long long)k * rg.DX[1];
+    long long Z = rg.X0[2] + (long long)k * rg.DX[2];
+    return X >= 0 && (X >> 32) < G.nx - 1 && Y >= 0 && (Y >> 32) < G.ny - 1 && Z >= 0 && (Z >> 32) < G.nz - 1;
+}
+
+// State of the run a lane is walking.
+struct LaneRun {
+    long long X, Y, Z, dX, dY, dZ;
+    const float *gz;
+    int k, k1;          // next sample, last sample
+    bool clamp;         // the run leaves the volume somewhere
+};
+
+__device__ __forceinline__ void lane_start(LaneRun &L, const Run &run, const RayGeo &rg, const float *gz,
+                                           const GatherArgs &G)
+{
+    L.k = run.k0;
+    L.k1 = run.k1;
+    L.X = rg.X0[0] + (long long)run.k0 * rg.DX[0];
+    L.Y = rg.X0[1] + (long long)run.k0 * rg.DX[1];
+    L.Z = rg.X0[2] + (long long)run.k0 * rg.DX[2];
+    L.dX = rg.DX[0];
+    L.dY = rg.DX[1];
+    L.dZ = rg.DX[2];
+    L.gz = gz;
+    L.clamp = !(inside_all(rg, G, run.k0) && inside_all(rg, G, run.k1));
+}
+
+// Gather the runs [q0, q1) of one brick (first cell (bx0, by0, bz0)) into
+// this warp's 9^3 accumulator.  Each lane walks one run; per warp step it
+// advances up to kGSteps samples while they stay in one cell and emits that
+// cell's record (its 8 corner sums).  The warp then sorts the 32 records by
+// (cell, lane) with a shuffle bitonic network, ranks equal cells, and writes
+// rank by rank, one corner at a time: within a rank all cells differ, and for
+// a fixed corner offset distinct cells hit distinct voxels.  A lane whose run
+// ends takes the next run in order, so every decision depends only on the
+// data and the sums have a fixed order.
+__device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const uint32_t *__restrict__ order,
+                                            uint32_t q0, uint32_t q1, const RayGeo *__restrict__ geo,
+                                            const float *__restrict__ gzbuf, const long long *__restrict__ gz_off,
+                                            const GatherArgs &G, int bx0, int by0, int bz0, GatherSmem &sm, int w)
 {
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     float *acc = sm.acc[w];
-    for (int k0 = k0r; k0 <= k1r; k0 += 32 * kChunk) {
-        const int ks = k0 + lane * kChunk;
-        long long X = rg.X0[0] + (long long)ks * rg.DX[0];
-        long long Y = rg.X0[1] + (long long)ks * rg.DX[1];
-        long long Z = rg.X0[2] + (long long)ks * rg.DX[2];
-        int nr = 0;
-        int cur = -1;
+    LaneRun L;
+    bool active = false;
+    uint32_t next = q0;           // next unassigned run (warp-uniform)
+    for (;;) {
+        // refill idle lanes in lane order
+        const unsigned need = __ballot_sync(0xffffffffu, !active);
+        if (need) {
+            const uint32_t mine = next + __popc(need & lt);
+            if (!active && mine < q1) {
+                const Run run = runs[order[mine]];
+                const RayGeo rg = geo[run.ray];
+                lane_start(L, run, rg, gzbuf + gz_off[run.ray], G);
+                active = true;
+            }
+            next += __popc(need);
+        }
+        if (!__any_sync(0xffffffffu, active)) break;
+        // advance up to kGSteps samples within one cell
+        int cell = -1;
         float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        bool more = active;
 #pragma unroll
-        for (int t = 0; t < kChunk; t++) {
-            const int k = ks + t;
-            if (k <= k1r) {
+        for (int t = 0; t < kGSteps; t++) {
+            if (more) {
                 int ix, iy, iz;
                 float fx, fy, fz;
-                bool i0, i1, i2;
-                axis_split(X, G.nx, ix, fx, i0);
-                axis_split(Y, G.ny, iy, fy, i1);
-                axis_split(Z, G.nz, iz, fz, i2);
-                const float g = __ldg(gz + k);
-                const int cell = (ix - bx0) | ((iy - by0) << 4) | ((iz - bz0) << 8);
-                if (cell != cur) {
-                    if (cur >= 0) {
-#pragma unroll
-                        for (int q = 0; q < 8; q++) sm.rec[w][nr][q][lane] = v[q];
-                        sm.reccell[w][nr][lane] = cur;
-                        nr++;
-                    }
-                    cur = cell;
-#pragma unroll
-                    for (int q = 0; q < 8; q++) v[q] = 0.0f;
+                if (L.clamp) {
+                    gather_axis<true>(L.X, G.nx, ix, fx);
+                    gather_axis<true>(L.Y, G.ny, iy, fy);
+                    gather_axis<true>(L.Z, G.nz, iz, fz);
+                } else {
+                    gather_axis<false>(L.X, G.nx, ix, fx);
+                    gather_axis<false>(L.Y, G.ny, iy, fy);
+                    gather_axis<false>(L.Z, G.nz, iz, fz);
                 }
-                const float wx1 = fx, wx0 = 1.0f - fx, wy1 = fy, wy0 = 1.0f - fy;
-                const float gz0 = g * (1.0f - fz), gz1 = g * fz;
-                const float a00 = gz0 * wy0, a10 = gz0 * wy1, a01 = gz1 * wy0, a11 = gz1 * wy1;
-                v[0] = fmaf(a00, wx0, v[0]); v[1] = fmaf(a00, wx1, v[1]);
-                v[2] = fmaf(a10, wx0, v[2]); v[3] = fmaf(a10, wx1, v[3]);
-                v[4] = fmaf(a01, wx0, v[4]); v[5] = fmaf(a01, wx1, v[5]);
-                v[6] = fmaf(a11, wx0, v[6]); v[7] = fmaf(a11, wx1, v[7]);
+                const int c = (ix - bx0) | ((iy - by0) << 4) | ((iz - bz0) << 8);
+                if (cell >= 0 && c != cell) {
+                    more = false;            // the next record starts here
+                } else {
+                    cell = c;
+                    const float g = __ldg(L.gz + L.k);
+                    const float wx1 = fx, wx0 = 1.0f - fx, wy1 = fy, wy0 = 1.0f - fy;
+                    const float gz0 = g * (1.0f - fz), gz1 = g * fz;
+                    const float a00 = gz0 * wy0, a10 = gz0 * wy1, a01 = gz1 * wy0, a11 = gz1 * wy1;
+                    v[0] = fmaf(a00, wx0, v[0]); v[1] = fmaf(a00, wx1, v[1]);
+                    v[2] = fmaf(a10, wx0, v[2]); v[3] = fmaf(a10, wx1, v[3]);
+                    v[4] = fmaf(a01, wx0, v[4]); v[5] = fmaf(a01, wx1, v[5]);
+                    v[6] = fmaf(a11, wx0, v[6]); v[7] = fmaf(a11, wx1, v[7]);
+                    L.X += L.dX;
+                    L.Y += L.dY;
+                    L.Z += L.dZ;
+                    L.k++;
+                    if (L.k > L.k1) {
+                        more = false;
+                        active = false;
+                    }
+                }
             }
-            X += rg.DX[0];
-            Y += rg.DX[1];
-            Z += rg.DX[2];
         }
-        if (cur >= 0) {
+        // record of this lane: cell (0..7 per axis) packed into 9 bits
+        const int cl = cell >= 0 ? ((cell & 7) | (((cell >> 4) & 7) << 3) | (((cell >> 8) & 7) << 6)) : 1023;
 #pragma unroll
-            for (int q = 0; q < 8; q++) sm.rec[w][nr][q][lane] = v[q];
-            sm.reccell[w][nr][lane] = cur;
-            nr++;
+        for (int q = 0; q < 8; q++) sm.rec[w][q][lane] = v[q];
+        // bitonic sort of (cell << 5 | lane), unique keys, ascending
+        unsigned key = ((unsigned)cl << 5) | (unsigned)lane;
+#pragma unroll
+        for (int k2 = 2; k2 <= 32; k2 <<= 1) {
+#pragma unroll
+            for (int j = k2 >> 1; j > 0; j >>= 1) {
+                const unsigned other = __shfl_xor_sync(0xffffffffu, key, j);
+                const bool up = ((lane & k2) == 0);
+                const bool lower = (lane & j) == 0;
+                const unsigned lo = min(key, other), hi = max(key, other);
+                key = (lower == up) ? lo : hi;
+            }
         }
+        const int scell = (int)(key >> 5), src = (int)(key & 31);
+        const int prev_cell = __shfl_up_sync(0xffffffffu, scell, 1);
+        // rank = position within the group of equal cells
+        const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev_cell != scell);
+        const int rank = lane - (31 - __clz(heads & (0xffffffffu >> (31 - lane))));
+        const bool valid = scell != 1023;
+        const int max_rank = (int)__reduce_max_sync(0xffffffffu, valid ? (unsigned)rank : 0u);
         __syncwarp();
-        // ranks of the chain heads: my first record continues the previous
-        // lane's last record when both name the same cell
-        const int first = nr > 0 ? sm.reccell[w][0][lane] : -1;
-        const int last = nr > 0 ? sm.reccell[w][nr - 1][lane] : -2;
-        const int prev_last = __shfl_up_sync(0xffffffffu, last, 1);
-        const bool cont = lane > 0 && nr > 0 && first == prev_last;
-        int rank_first = cont ? 1 : 0;
-        for (;;) {
-            // a lane holding a single record passes its rank on as its last
-            const int rank_last = nr == 1 ? rank_first : 0;
-            const int prev = __shfl_up_sync(0xffffffffu, rank_last, 1);
-            const int nf = cont ? prev + 1 : 0;
-            const bool changed = nf != rank_first;
-            rank_first = nf;
-            if (!__any_sync(0xffffffffu, changed)) break;
-        }
-        int max_rank = rank_first;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) max_rank = max(max_rank, __shfl_xor_sync(0xffffffffu, max_rank, off));
+        const int cx = scell & 7, cy = (scell >> 3) & 7, cz = scell >> 6;
+        const int base = (cz * kBrickV + cy) * kBrickV + cx;
         for (int pass = 0; pass <= max_rank; pass++) {
-            const int r0 = (pass == 0) ? (rank_first == 0 ? 0 : 1) : 0;
-            const int r1 = (pass == 0) ? nr : ((rank_first == pass && nr > 0) ? 1 : 0);
-            // one corner at a time: within a corner every write of the warp
-            // goes to a distinct voxel; __syncwarp orders the corners
+            const bool mine = valid && rank == pass;
 #pragma unroll
             for (int q = 0; q < 8; q++) {
-                const int off = ((q >> 2) * kBrickV + ((q >> 1) & 1)) * kBrickV + (q & 1);
-                for (int r = r0; r < r1; r++) {
-                    const int c = sm.reccell[w][r][lane];
-                    const int cx = c & 15, cy = (c >> 4) & 15, cz = c >> 8;
-                    acc[(cz * kBrickV + cy) * kBrickV + cx + off] += sm.rec[w][r][q][lane];
+                if (mine) {
+                    const int off = ((q >> 2) * kBrickV + ((q >> 1) & 1)) * kBrickV + (q & 1);
+                    acc[base + off] += sm.rec[w][q][src];
                 }
                 __syncwarp();
             }

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) k_march_fwd(const T *__restric
     const int j = blockIdx.x * kWarpsFwd + w;
     if (j >= n_rays) return;
     RayGeo rg = geo[j];
-    RayOut o{out + (size_t)j * rg.S, valid ? valid + j : nullptr, status, nullptr};
+    RayOut o{out + (size_t)j * rg.S, valid ? valid + j : nullptr, status, nullptr, nullptr};
     march_fwd_ray<T>(vol, A, rg, o, buf[w]);
 }
 

@@ -33,6 +33,7 @@ struct RayOut {
     int *valid;       // nullable: leading pole-free rows
     uint32_t *status; // nullable
     float4 *ckpt;     // nullable: scan carry (b0, b1, D) at every segment start, for the adjoint
+    float *mrow;      // nullable: speckle factor of every row, for the adjoint
 };
 
 __device__ __forceinline__ int smem_idx(int x) { return x + (x >> 3); }
@@ -54,15 +55,17 @@ __device__ __forceinline__ void seg_reflections(const T *__restrict__ vol, const
     const int lane = threadIdx.x & 31;
     const int S = rg.S;
     float pzr = czr, pdz = cdz;
+    long long X, Y, Z;
+    sample_pos(rg, base + lane + 1, X, Y, Z);
+    const long long sX = rg.DX[0] * kWarp, sY = rg.DX[1] * kWarp, sZ = rg.DX[2] * kWarp;
 #pragma unroll
     for (int t = 0; t < kChunk; t++) {
         int k = base + t * kWarp + lane + 1;
         float zr = 0.0f, dz = 0.0f;
-        if (k <= S) {
-            long long X, Y, Z;
-            sample_pos(rg, k, X, Y, Z);
-            sample_z<T, false>(vol, g, X, Y, Z, zr, dz);
-        }
+        if (k <= S) sample_z<T, false>(vol, g, X, Y, Z, zr, dz);
+        X += sX;
+        Y += sY;
+        Z += sZ;
         float lzr = __shfl_up_sync(0xffffffffu, zr, 1);
         float ldz = __shfl_up_sync(0xffffffffu, dz, 1);
         if (lane == 0) { lzr = pzr; ldz = pdz; }
@@ -223,6 +226,11 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
 #pragma unroll
             for (int t = 0; t < kChunk; t++) m[t] = 1.0f;
         }
+        if (out.mrow) {
+#pragma unroll
+            for (int t = 0; t < kChunk; t++)
+                if (i0 + t < S) out.mrow[i0 + t] = m[t];
+        }
         float y[kChunk];
 #pragma unroll
         for (int t = 0; t < kChunk; t++) {
@@ -231,7 +239,7 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
             if (i < S) {
                 Xfer x = xfer(rr[t], A.a2, A.mode);
                 float q = fmaf(b0, x.m01, b1);          // det(A_{i+1})
-                float e = x.m01 * D * __frcp_rn(b1 * q);
+                float e = x.m01 * D * frcp(b1 * q);
                 if (!(q >= kPoleEps)) first_bad = min(first_bad, i + 1);
                 float nb0 = fmaf(b0, x.m00, b1 * x.m10);
                 b1 = q;

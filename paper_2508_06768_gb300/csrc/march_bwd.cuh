@@ -35,7 +35,7 @@ __device__ __forceinline__ EchoGrad echo_grad(float b0, float b1, float D, float
 {
     if (ge == 0.0f) return {0.0f, 0.0f, 0.0f, 0.0f};   // masked rows (e.g. past a pole) add nothing
     float q = fmaf(b0, x, b1);
-    float iq = __frcp_rn(q), ib1 = __frcp_rn(b1);
+    float iq = frcp(q), ib1 = frcp(b1);
     float e = x * D * ib1 * iq;
     EchoGrad g;
     g.gb0 = -ge * e * x * iq;
@@ -47,11 +47,13 @@ __device__ __forceinline__ EchoGrad echo_grad(float b0, float b1, float D, float
 
 // have_ckpt: the forward march of the same call already wrote the segment
 // carries into ckpt, so the recording sweep is skipped.
+// mrow: speckle factors written by the forward of the same call (nullable;
+// recomputed from Philox when absent).
 template <typename T>
 __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, const RayGeo &rg,
                               const float *__restrict__ gy_row, float *__restrict__ gz_row,
                               double *__restrict__ pose_part, float4 *__restrict__ ckpt, BwdSmem &sm,
-                              bool have_ckpt = false)
+                              bool have_ckpt = false, const float *__restrict__ mrow = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int S = rg.S;
@@ -96,16 +98,18 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
     for (int s = nseg - 1; s >= 0; s--) {
         const int base = s * kSeg;
         // A': samples base .. base+255 with gradients; sample base+256 carried
+        long long X, Y, Z;
+        sample_pos(rg, base + lane, X, Y, Z);
+        const long long sX = rg.DX[0] * kWarp, sY = rg.DX[1] * kWarp, sZ = rg.DX[2] * kWarp;
 #pragma unroll
         for (int t = 0; t < kChunk; t++) {
             int p = t * kWarp + lane;
             int k = base + p;
             float zr = 0.0f, dz = 0.0f, g3[3] = {0.0f, 0.0f, 0.0f};
-            if (k <= S) {
-                long long X, Y, Z;
-                sample_pos(rg, k, X, Y, Z);
-                sample_z<T, true>(vol, A.g, X, Y, Z, zr, dz, g3);
-            }
+            if (k <= S) sample_z<T, true>(vol, A.g, X, Y, Z, zr, dz, g3);
+            X += sX;
+            Y += sY;
+            Z += sZ;
             int o = smem_idx(p);
             sm.zr[o] = zr; sm.dz[o] = dz; sm.gx[o] = g3[0]; sm.gy[o] = g3[1]; sm.gz[o] = g3[2];
         }
@@ -128,12 +132,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
 
         // B': reflection coefficients of this lane's chunk and the forward scan
         const int i0 = base + lane * kChunk;
-        float rr[kChunk], Zs[kChunk + 1];
-#pragma unroll
-        for (int t = 0; t <= kChunk; t++) {
-            int o = smem_idx(lane * kChunk + t);
-            Zs[t] = sm.zr[o] + sm.dz[o];
-        }
+        float rr[kChunk];
 #pragma unroll
         for (int t = 0; t < kChunk; t++) {
             int o = smem_idx(lane * kChunk + t), o1 = smem_idx(lane * kChunk + t + 1);
@@ -163,7 +162,10 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
         }
         // adjoint sources of the echo rows
         float m[kChunk];
-        if (A.sp.on) {
+        if (mrow) {
+#pragma unroll
+            for (int t = 0; t < kChunk; t++) m[t] = (i0 + t < S) ? __ldg(mrow + i0 + t) : 1.0f;
+        } else if (A.sp.on) {
             chunk_speckle(A.sp, i0, S, rg.ray, pose, m);
         } else {
 #pragma unroll
@@ -228,13 +230,28 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
             }
         }
 
-        // E': true reverse pass: parameter adjoints -> dL/dr -> dL/dZ
-        float gzc[kChunk], gzn[kChunk];
+        // E': true reverse pass: parameter adjoints -> dL/dr -> dL/dZ.
+        // dL/dZ of sample i0+t+1 (t < 7) is complete once interfaces t and
+        // t+1 are done, so it is finalised inside the loop; sample i0+8 also
+        // needs the next lane's interface and is finalised after it.
         const float a2 = A.a2;
+        float a[6] = {0, 0, 0, 0, 0, 0};
+        float c_next = 0.0f;     // Z1-role contribution of interface t+1 to sample i0+t+1
+        float n_last = 0.0f;     // Z2-role contribution of interface i0+7 to sample i0+8
+        float c_first = 0.0f;    // Z1-role contribution of interface i0 to sample i0
+        auto add_pose = [&](int k, int o, float G) {
+            const float gx = sm.gx[o], gyv = sm.gy[o], gzv = sm.gz[o];
+            const float sk = ((float)k + 0.5f) * ds;
+            a[0] = fmaf(G, gx, a[0]);
+            a[1] = fmaf(G, gyv, a[1]);
+            a[2] = fmaf(G, gzv, a[2]);
+            a[3] = fmaf(G * sk, gx, a[3]);
+            a[4] = fmaf(G * sk, gyv, a[4]);
+            a[5] = fmaf(G * sk, gzv, a[5]);
+        };
 #pragma unroll
         for (int t = kChunk - 1; t >= 0; t--) {
-            gzc[t] = 0.0f;
-            gzn[t] = 0.0f;
+            float gzc = 0.0f, gzn = 0.0f;
             if (i0 + t < S) {
                 const float r = rr[t];
                 Xfer x = xfer(r, a2, A.mode);
@@ -254,58 +271,52 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                 lmu = fmaf(lmu, x.delta, g.gD);
                 le0 = n0;
                 le1 = n1;
-                float z1 = Zs[t], z2 = Zs[t + 1], sz = z1 + z2;
-                float is2 = __frcp_rn(sz * sz);
-                gzc[t] = gr * (-2.0f * z2) * is2;
-                gzn[t] = gr * (2.0f * z1) * is2;
+                const int o1 = smem_idx(lane * kChunk + t), o2 = smem_idx(lane * kChunk + t + 1);
+                const float z1 = sm.zr[o1] + sm.dz[o1], z2 = sm.zr[o2] + sm.dz[o2], sz = z1 + z2;
+                const float is2 = frcp(sz * sz);
+                gzc = gr * (-2.0f * z2) * is2;
+                gzn = gr * (2.0f * z1) * is2;
             }
+            if (t == kChunk - 1) {
+                n_last = gzn;
+            } else {
+                const int k = i0 + t + 1;
+                if (k <= S) {
+                    const float G = c_next + gzn;
+                    gz_row[k] = G;
+                    add_pose(k, smem_idx(lane * kChunk + t + 1), G);
+                }
+            }
+            c_next = gzc;
+            if (t == 0) c_first = gzc;
         }
         // adjoint at the segment start for the earlier segment
         lam0 = __shfl_sync(0xffffffffu, le0, 0);
         lam1 = __shfl_sync(0xffffffffu, le1, 0);
         mus = __shfl_sync(0xffffffffu, lmu, 0);
 
-        // F': finalise dL/dZ of samples i0+1 .. i0+8 (and sample 0)
-        float nextc = __shfl_down_sync(0xffffffffu, gzc[0], 1);
-        if (lane == kWarp - 1) nextc = carry_gz1;
-        float first_c = __shfl_sync(0xffffffffu, gzc[0], 0);
-        float a[6] = {0, 0, 0, 0, 0, 0};
-#pragma unroll
-        for (int t = 1; t <= kChunk; t++) {
-            int k = i0 + t;
-            float G = (t < kChunk) ? gzc[t] + gzn[t - 1] : gzn[kChunk - 1] + nextc;
+        // F': sample i0+8 (the next lane's first sample) and sample 0
+        {
+            float nextc = __shfl_down_sync(0xffffffffu, c_first, 1);
+            if (lane == kWarp - 1) nextc = carry_gz1;
+            const int k = i0 + kChunk;
             if (k <= S) {
+                const float G = n_last + nextc;
                 gz_row[k] = G;
-                int o = smem_idx(lane * kChunk + t);
-                float gx = sm.gx[o], gyv = sm.gy[o], gzv = sm.gz[o];
-                float sk = ((float)k + 0.5f) * ds;
-                a[0] = fmaf(G, gx, a[0]);
-                a[1] = fmaf(G, gyv, a[1]);
-                a[2] = fmaf(G, gzv, a[2]);
-                a[3] = fmaf(G * sk, gx, a[3]);
-                a[4] = fmaf(G * sk, gyv, a[4]);
-                a[5] = fmaf(G * sk, gzv, a[5]);
+                add_pose(k, smem_idx(lane * kChunk + kChunk), G);
             }
         }
         if (s == 0 && lane == 0) {
-            float G = gzc[0];
-            gz_row[0] = G;
-            int o = smem_idx(0);
-            float sk = 0.5f * ds;
-            a[0] = fmaf(G, sm.gx[o], a[0]);
-            a[1] = fmaf(G, sm.gy[o], a[1]);
-            a[2] = fmaf(G, sm.gz[o], a[2]);
-            a[3] = fmaf(G * sk, sm.gx[o], a[3]);
-            a[4] = fmaf(G * sk, sm.gy[o], a[4]);
-            a[5] = fmaf(G * sk, sm.gz[o], a[5]);
+            gz_row[0] = c_first;
+            add_pose(0, smem_idx(0), c_first);
         }
-        carry_gz1 = first_c;
+        carry_gz1 = __shfl_sync(0xffffffffu, c_first, 0);
 #pragma unroll
         for (int q = 0; q < 6; q++) {
             float v = a[q];
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            acc[q] += (double)v;
+            if (lane == 0) acc[q] += (double)v;
         }
         __syncwarp();
     }
