@@ -116,23 +116,91 @@ def build_workload(rank=0, count=512, n=256):
     return vol, poses[:count], fans[:count], prm
 
 
-# Algorithmic HBM bytes per ray-sample of each phase (see the design notes):
-# the image row written by the forward march, the pre-blur rows read and the
-# image written by the blur, the adjoint march reading dL/dimage-after-blur
-# transpose and writing dL/dZ, and the gather reading dL/dZ once.
-ALGO_BYTES = {"march_fwd": 4.0, "blur": 8.0, "blur_T": 8.0, "march_bwd": 8.0, "gather": 4.0}
+# Kernels of one batched step, with the phase events that bracket them:
+# name -> (first event, last event) of diffus_render_batch's trace.
+TRACE = {"ray_setup": (0, 1), "march_fwd": (1, 2), "blur": (2, 3), "blur_T": (3, 4), "march_bwd": (4, 5),
+         "pose_reduce": (5, 6), "gather_sort": (6, 8), "gather_units": (8, 9), "voxel_reduce": (9, 7)}
+N_EVENTS = 10
+
+# Algorithmic work per ray-sample of each kernel (derivation in the design
+# notes): HBM bytes that the method must move, and lane operations that it
+# must execute (trilinear sample, Eq. 1 coefficient, 2x2 step, echo,
+# Philox speckle; the adjoint adds the sampled gradient, the reverse scan
+# and the pose chain rule; the gather adds the 8 corner weights).
+ALGO_BYTES = {"march_fwd": 4.0, "blur": 8.0, "blur_T": 8.0, "march_bwd": 8.0, "gather_units": 4.0}
+ALGO_OPS = {"march_fwd": 111.0, "march_bwd": 135.0, "gather_units": 30.0}
+BOUND = {"march_fwd": "alu", "march_bwd": "alu", "gather_units": "alu", "blur": "hbm", "blur_T": "hbm"}
+# DRAM bytes per ray-sample measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch over the 64-pose prefix of the
+# workload, divided by its ray-samples); absent where the kernel changed since.
+NCU_DRAM_PER_UNIT = {}
 
 
-def cpu_sample(vol, poses, fans, prm, max_rays=24):
-    """The bounded CPU sample: forward+backward of the central max_rays rays
-    (same angular pitch) of the pose with the median ray-sample count."""
-    work = [f.n_rays * f.n_samples for f in fans]
-    p = int(np.argsort(work)[len(work) // 2])
-    f = fans[p]
-    m = min(max_rays, f.n_rays)
-    pitch = f.fov / max(f.n_rays - 1, 1)
-    sub = I.Fan(m, f.n_samples, pitch * (m - 1), f.depth, f.f_mhz, f.alpha)
-    return p, sub
+def median_pose_order(fans):
+    """Poses ordered by closeness of their ray-sample count to the median."""
+    work = np.array([f.n_rays * f.n_samples for f in fans], dtype=np.float64)
+    med = np.median(work)
+    return [int(i) for i in np.lexsort((np.arange(len(fans)), np.abs(work - med)))]
+
+
+def cpu_leg(vol, poses, fans, prm, budget_s=10.0, max_poses=8, images=None, grad_poses=None, G=None, offsets=None):
+    """The FP64 oracle, as it stands, on whole poses of the workload (those
+    nearest the median size), forward+backward, until budget_s has passed.
+    With the GPU results of the same poses, also returns their error
+    against the oracle (images over well-posed, well-conditioned rows;
+    pose gradients)."""
+    import oracle
+    order = median_pose_order(fans)
+    t_total, units, done = 0.0, 0, []
+    err_num = err_den = 0.0
+    gp_num = gp_den = 0.0
+    rows_used = rows_all = 0
+    W = oracle.blur_halfwidth(prm) if prm.blur else 0
+    for p in order[:max_poses]:
+        f = fans[p]
+        if G is not None:
+            Gp = G[int(offsets[p]):int(offsets[p + 1])].reshape(f.n_rays, f.n_samples).astype(np.float64)
+        else:
+            Gp = I.random_weights((f.n_rays, f.n_samples), 99).astype(np.float64)
+        t0 = time.perf_counter()
+        img, first, det = oracle.render(vol, poses[p], f, prm, pose_ctr=p, first_bad=True, dets=True)
+        _, gpose = oracle.render_grad(vol, poses[p], f, prm, Gp, pose_ctr=p, want_vol=False)
+        t_total += time.perf_counter() - t0
+        units += f.n_rays * f.n_samples
+        done.append(p)
+        if images is not None:
+            gimg = images[int(offsets[p]):int(offsets[p + 1])].reshape(f.n_rays, f.n_samples)
+            md = np.minimum(det[:, :-1], det[:, 1:])
+            ok = np.arange(f.n_samples)[None, :] < np.minimum(first - 1, f.n_samples)[:, None]
+            ok &= md >= 0.05
+            if W:
+                # a blurred row mixes rays j-W..j+W: all of them must qualify
+                okw = ok.copy()
+                for d in range(1, W + 1):
+                    okw[d:] &= ok[:-d]
+                    okw[:-d] &= ok[d:]
+                ok = okw
+            err_num += float(np.sum((gimg[ok] - img[ok]) ** 2))
+            err_den += float(np.sum(img[ok] ** 2))
+            rows_used += int(ok.sum())
+            rows_all += ok.size
+        if grad_poses is not None:
+            gp_num += float(np.sum((grad_poses[p] - gpose) ** 2))
+            gp_den += float(np.sum(gpose ** 2))
+        if t_total >= budget_s:
+            break
+    res = {"value": units / t_total, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": "%d whole poses of the workload nearest the median size (%s), %d ray-samples, "
+                     "forward+backward (pose gradient), FP64 oracle, %.1f s"
+                     % (len(done), ",".join(map(str, done)), units, t_total)}
+    err = None
+    if images is not None:
+        err = {"image_rel_l2": math.sqrt(err_num / err_den) if err_den > 0 else None,
+               "image_rows_compared": rows_used / max(rows_all, 1),
+               "grad_pose_rel_l2": math.sqrt(gp_num / gp_den) if gp_den > 0 else None,
+               "poses": done,
+               "rows": "rows before the first pole with min(det A_k, det A_k+1) >= 0.05 over the blur window"}
+    return res, err
 
 
 def run_reference(args):
@@ -141,12 +209,13 @@ def run_reference(args):
         return 0
     import oracle
     vol, poses, fans, prm = build_workload(0)
-    p, sub = cpu_sample(vol, poses, fans, prm)
-    G = I.random_weights((sub.n_rays, sub.n_samples), 99).astype(np.float64)
+    p = median_pose_order(fans)[0]
+    f = fans[p]
+    G = I.random_weights((f.n_rays, f.n_samples), 99).astype(np.float64)
 
     def step():
-        img, _ = oracle.render(vol, poses[p], sub, prm, pose_ctr=p)
-        oracle.render_grad(vol, poses[p], sub, prm, G, pose_ctr=p)
+        oracle.render(vol, poses[p], f, prm, pose_ctr=p)
+        oracle.render_grad(vol, poses[p], f, prm, G, pose_ctr=p)
 
     for _ in range(args.warmup):
         step()
@@ -154,10 +223,10 @@ def run_reference(args):
     for _ in range(args.steps):
         step()
     dt = (time.perf_counter() - t0) / args.steps
-    units = sub.n_rays * sub.n_samples
+    units = f.n_rays * f.n_samples
     val = units / dt
-    sample = ("pose %d: central %d rays x %d samples (of %d rays), forward+backward, FP64 oracle"
-              % (p, sub.n_rays, sub.n_samples, fans[p].n_rays))
+    sample = ("pose %d of the workload (the median size): %d rays x %d samples, forward+backward, FP64 oracle"
+              % (p, f.n_rays, f.n_samples))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -167,6 +236,100 @@ def run_reference(args):
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _time_graph(torch, graph, flush, stream, steps, warmup):
+    for _ in range(warmup):
+        flush.zero_()
+        graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
+def _capture(torch, fn):
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        fn(s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        fn(s)
+    torch.cuda.synchronize()
+    return g
+
+
+def run_forms(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, stream, steps, warmup, total):
+    """The batched form against the plain single-pose kernel, and the other
+    forms: forward only, speckle-off forward, BF16 volume."""
+    from dataclasses import replace
+    from paper_2508_06768_gb300.render import BatchRenderer
+    out = {}
+    dev = vol_d.device
+    # batched forward only
+    rf = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm, schedule=sched, with_bwd=False)
+    g = _capture(torch, lambda s: rf.run(poses_d, None, stream=s))
+    ms = _time_graph(torch, g, flush, stream, steps, warmup)
+    out["batched_fwd"] = {"value": total / (ms * 1e-3), "ms": ms}
+    fwd_ms = ms
+    del g, rf
+    # batched forward, speckle and blur off (the form closest to bandwidth-bound)
+    prm0 = replace(prm, speckle=0, blur=0)
+    rf = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm0, schedule=sched, with_bwd=False)
+    g = _capture(torch, lambda s: rf.run(poses_d, None, stream=s))
+    ms = _time_graph(torch, g, flush, stream, steps, warmup)
+    out["batched_fwd_no_speckle_no_blur"] = {"value": total / (ms * 1e-3), "ms": ms}
+    del g, rf
+    # BF16 volume, FP32 march, forward+backward
+    vb = vol_d.to(torch.bfloat16)
+    rb = BatchRenderer(vb, vol.spacing, vol.origin, fans, prm, schedule=sched, with_bwd=True)
+    g = _capture(torch, lambda s: rb.run(poses_d, G, stream=s))
+    ms = _time_graph(torch, g, flush, stream, steps, warmup)
+    out["batched_fwd_bwd_bf16_volume"] = {"value": total / (ms * 1e-3), "ms": ms}
+    del g, rb, vb
+    # plain single-pose kernel: diffus_render_fwd + diffus_render_bwd per pose
+    offs = np.concatenate([[0], np.cumsum([f.n_rays * f.n_samples for f in fans])])
+    vd = B.volume_desc(vol_d, vol.spacing, vol.origin)
+    wsb = max(B.workspace_bytes(vd, B.fan_desc(f), B.params_desc(prm, p), True) for p, f in enumerate(fans))
+    wsp = B.alloc_workspace(wsb, dev)
+    img = torch.empty(int(offs[-1]), dtype=torch.float32, device=dev)
+    rv = torch.empty(max(f.n_rays for f in fans), dtype=torch.int32, device=dev)
+    st = torch.zeros(4, dtype=torch.int32, device=dev)
+    gv = torch.empty(vol_d.shape, dtype=torch.float32, device=dev)
+    gp = torch.empty((len(fans), 6), dtype=torch.float32, device=dev)
+
+    def plain(s, bwd):
+        for p, f in enumerate(fans):
+            im = img[int(offs[p]):int(offs[p + 1])].view(f.n_rays, f.n_samples)
+            B.render_fwd(vol_d, vol.spacing, vol.origin, poses_d[p], f, prm, image=im, ray_valid=rv[:f.n_rays],
+                         status=st, workspace=wsp, stream=s, pose_ctr=p)
+            if bwd:
+                gi = G[int(offs[p]):int(offs[p + 1])].view(f.n_rays, f.n_samples)
+                B.render_bwd(vol_d, vol.spacing, vol.origin, poses_d[p], f, prm, gi, grad_vol=gv, grad_pose=gp[p],
+                             status=st, workspace=wsp, stream=s, pose_ctr=p)
+
+    g = _capture(torch, lambda s: plain(s, False))
+    ms = _time_graph(torch, g, flush, stream, max(1, min(steps, 3)), 1)
+    out["plain_fwd"] = {"value": total / (ms * 1e-3), "ms": ms}
+    del g
+    g = _capture(torch, lambda s: plain(s, True))
+    ms = _time_graph(torch, g, flush, stream, max(1, min(steps, 3)), 1)
+    out["plain_fwd_bwd"] = {"value": total / (ms * 1e-3), "ms": ms,
+                            "note": "one diffus_render_fwd and one diffus_render_bwd per pose, graph-captured; "
+                                    "per-pose volume gradients are not summed"}
+    del g
+    out["speedup_fwd_vs_plain"] = out["plain_fwd"]["ms"] / fwd_ms
+    return out
 
 
 def run_native(args):
@@ -196,7 +359,7 @@ def run_native(args):
                             candidates=[(4, 4, 8), (8, 2, 8), (4, 6, 4), (2, 8, 8)], reps=1)
     r = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm, schedule=sched, with_bwd=True)
 
-    events = [torch.cuda.Event(enable_timing=True) for _ in range(8)]
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(N_EVENTS)]
     for e in events:
         e.record()   # torch creates the underlying CUDA event lazily
     torch.cuda.synchronize()
@@ -211,7 +374,7 @@ def run_native(args):
         flush.zero_()
         graph.replay()
     torch.cuda.synchronize()
-    phase_ms = np.zeros(7)
+    kern_ms = {k: 0.0 for k in TRACE}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if ws > 1:
         dist.barrier()
@@ -225,8 +388,8 @@ def run_native(args):
             e1.record(stream)
             torch.cuda.synchronize()
             total_ms += e0.elapsed_time(e1)
-            for i in range(7):
-                phase_ms[i] += events[i].elapsed_time(events[i + 1])
+            for k, (a, b) in TRACE.items():
+                kern_ms[k] += events[a].elapsed_time(events[b])
     torch.cuda.synchronize()
     if ws > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -235,8 +398,11 @@ def run_native(args):
         dist.barrier()
     ms_per_step = total_ms / args.steps
     value = total * ws / (ms_per_step * 1e-3)
-    phase_ms /= args.steps
+    kern_ms = {k: v / args.steps for k, v in kern_ms.items()}
     status = r.status.cpu().numpy().view(np.uint32)
+    clocks = clk.summary()
+    images_h = r.images.cpu().numpy()
+    gposes_h = r.grad_poses.cpu().numpy()
 
     # ---- end to end through the public API: host buffers, copies inside the timed region
     e2e = None
@@ -269,30 +435,55 @@ def run_native(args):
         e2e = {"value": total * ws / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
 
-    # ---- roofline of the dominant phase
-    names = ["ray_setup", "march_fwd", "blur", "blur_T", "march_bwd", "pose_reduce", "gather"]
-    dom = int(np.argmax(phase_ms))
+    # ---- forms: batched vs the plain single-pose kernel, forward only, speckle off, BF16
+    forms = None
+    if not args.no_forms:
+        forms = run_forms(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, stream, args.steps,
+                          args.warmup, total)
+        forms["batched_fwd_bwd"] = {"value": total / (ms_per_step * 1e-3), "ms": ms_per_step}
+        forms["speedup_fwd_bwd_vs_plain"] = forms["plain_fwd_bwd"]["ms"] / ms_per_step
+
+    # ---- roofline of the dominant kernel (algorithmic work / event-timed duration)
     peaks = _peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    bytes_per = ALGO_BYTES.get(names[dom], 4.0) * total
-    achieved = bytes_per / (phase_ms[dom] * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None,
-            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = clocks["sm_mhz"] or 2070.0
+    alu_peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e12   # T lane-op/s
+    timed = {k: v for k, v in kern_ms.items() if k in BOUND}
+    dom = max(timed, key=timed.get)
+    t_dom = kern_ms[dom] * 1e-3
+    dram = NCU_DRAM_PER_UNIT.get(dom)
+    if BOUND[dom] == "alu":
+        ach = ALGO_OPS[dom] * total / t_dom / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": alu_peak, "unit": "Tlane-op/s",
+                "frac": ach / alu_peak, "traffic": None if dram is None else dram * total,
+                "peak_source": "derived: %d SMs x 128 lanes x %.0f MHz" % (props.multi_processor_count, sm_mhz),
+                "ops_per_ray_sample": ALGO_OPS[dom]}
+    else:
+        ach = ALGO_BYTES[dom] * total / t_dom / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": None if dram is None else dram * total,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    roof["hbm_frac"] = ALGO_BYTES.get(dom, 4.0) * total / t_dom / 1e9 / hbm
+    # the batched forward as a whole against HBM (4 B of image per ray-sample)
+    fwd_ms = kern_ms["ray_setup"] + kern_ms["march_fwd"] + kern_ms["blur"]
+    roof_fwd = {"bound": "hbm", "achieved": 4.0 * total / (fwd_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": 4.0 * total / (fwd_ms * 1e-3) / 1e9 / hbm, "bytes_per_ray_sample": 4.0,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    kernels = {}
+    for k, v in kern_ms.items():
+        d = {"ms": v}
+        if k in ALGO_OPS:
+            d["alu_frac"] = ALGO_OPS[k] * total / (v * 1e-3) / 1e12 / alu_peak
+        if k in ALGO_BYTES:
+            d["hbm_frac"] = ALGO_BYTES[k] * total / (v * 1e-3) / 1e9 / hbm
+        kernels[k] = d
 
-    # ---- CPU baseline: the FP64 oracle on a bounded sample
-    cpu = None
+    # ---- CPU baseline: the FP64 oracle on a bounded sample, and the error of the same poses
+    cpu, err = None, None
     if rank == 0 and not args.no_cpu:
-        import oracle
-        p, sub = cpu_sample(vol, poses, fans, prm)
-        Gs = I.random_weights((sub.n_rays, sub.n_samples), 99).astype(np.float64)
-        t0 = time.perf_counter()
-        oracle.render(vol, poses[p], sub, prm, pose_ctr=p)
-        oracle.render_grad(vol, poses[p], sub, prm, Gs, pose_ctr=p)
-        dt = time.perf_counter() - t0
-        cpu = {"value": sub.n_rays * sub.n_samples / dt, "unit": UNIT, "cores": oracle.num_threads(),
-               "kind": "oracle", "sample": "pose %d: central %d rays x %d samples, forward+backward, %.1f s"
-                                           % (p, sub.n_rays, sub.n_samples, dt)}
+        cpu, err = cpu_leg(vol, poses, fans, prm, images=images_h, grad_poses=gposes_h,
+                           G=G.cpu().numpy(), offsets=r.offsets)
 
     # kernels per step: ray setup, forward march, blur, blur transpose,
     # adjoint march, pose reduction; gather: brick runs, 2 radix passes of
@@ -308,9 +499,10 @@ def run_native(args):
                            "l2": "flushed between steps (2x129 MB write)", "parallelism": "replicas (weak)",
                            "schedule": None if sched is None else [sched.rays_per_cta, sched.ctas_per_sm,
                                                                    sched.brick]},
-                "phases_ms": {n: float(v) for n, v in zip(names, phase_ms)},
+                "kernels": kernels,
                 "status": [int(x) for x in status],
-                "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+                "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+                "roofline_batched_fwd": roof_fwd, "forms": forms, "err_vs_fp64": err,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -327,6 +519,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--poses", type=int, default=512,
                     help="poses of the batch (512 = the full workload; fewer only for profiler captures)")
     args = ap.parse_args()

@@ -205,7 +205,9 @@ enum {
     DIFFUS_TR_POSE = 5,        /* after the adjoint march */
     DIFFUS_TR_GATHER = 6,      /* after the pose reduction */
     DIFFUS_TR_END = 7,         /* after the volume gather */
-    DIFFUS_TR_COUNT = 8
+    DIFFUS_TR_GATHER_UNITS = 8,  /* inside the gather: before the brick-unit kernel */
+    DIFFUS_TR_GATHER_REDUCE = 9, /* inside the gather: before the per-voxel reduction */
+    DIFFUS_TR_COUNT = 10
 };
 typedef struct {
     void *event[DIFFUS_TR_COUNT];

@@ -46,7 +46,7 @@ class ScheduleDesc(C.Structure):
 
 
 class TraceDesc(C.Structure):
-    _fields_ = [("event", C.c_void_p * 8)]
+    _fields_ = [("event", C.c_void_p * 10)]
 
 
 class DiffusError(RuntimeError):

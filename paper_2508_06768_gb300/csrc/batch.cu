@@ -16,11 +16,6 @@
 using namespace dfs;
 
 namespace dfs {
-MarchArgs make_march_args(const diffus_volume_desc *vd, const diffus_fan *fan, const diffus_params *prm);
-size_t gather_workspace_bytes(const diffus_volume_desc *vd, long long n_rays, double max_path_mm);
-int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_rays, double max_path_mm,
-                  const float *gz, const long long *gz_off, void *ws, uint32_t *status, float *grad_vol,
-                  int ctas_per_sm, cudaStream_t s);
 }  // namespace dfs
 
 namespace {
@@ -35,8 +30,8 @@ struct PlanPose {
     int64_t img_off;
 };
 
-struct BlurTile {
-    int32_t pose, j0, k0, pad;
+struct BlurTile {                 // one 32-row strip of one pose image
+    int32_t pose, n_rays, k0, pad;
 };
 
 struct PlanHeader {
@@ -101,8 +96,7 @@ PlanSizes plan_sizes(int P, int64_t total_rays, int64_t n_tiles)
 int64_t count_tiles(const diffus_fan *fans, int P)
 {
     int64_t t = 0;
-    for (int p = 0; p < P; p++)
-        t += (int64_t)((fans[p].n_samples + kBlurRows - 1) / kBlurRows) * ((fans[p].n_rays + kBlurRays - 1) / kBlurRays);
+    for (int p = 0; p < P; p++) t += (int64_t)((fans[p].n_samples + kBlurRows - 1) / kBlurRows);
     return t;
 }
 
@@ -210,19 +204,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch_bwd(const T *__restrict__ 
 }
 
 template <bool TRANSPOSE, int WT>
-__global__ void __launch_bounds__(kBlurThreads) k_batch_blur(const float *__restrict__ in, float *__restrict__ out,
-                                                             const PlanPose *__restrict__ poses,
-                                                             const BlurTile *__restrict__ tiles, int64_t n_tiles,
-                                                             BlurArgs b)
+__global__ void __launch_bounds__(kBlurWarps * 32) k_batch_blur(const float *__restrict__ in, float *__restrict__ out,
+                                                                const PlanPose *__restrict__ poses,
+                                                                const BlurTile *__restrict__ tiles, int64_t n_tiles,
+                                                                BlurArgs b)
 {
-    extern __shared__ float dyn[];
-    float *wsm = dyn;
-    float *sm = dyn + (kMaxW + 1) * 32;
-    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int64_t nw = (int64_t)gridDim.x * kBlurWarps;
+    for (int64_t t = (int64_t)blockIdx.x * kBlurWarps + (threadIdx.x >> 5); t < n_tiles; t += nw) {
         const BlurTile tl = tiles[t];
         const PlanPose pp = poses[tl.pose];
-        blur_tile<TRANSPOSE, WT>(in + pp.img_off, out + pp.img_off, pp.n_rays, pp.S, b, tl.j0, tl.k0, sm, wsm);
-        __syncthreads();
+        blur_strip<TRANSPOSE, WT>(in + pp.img_off, out + pp.img_off, pp.n_rays, pp.S, b, tl.k0);
     }
 }
 
@@ -230,13 +221,12 @@ template <bool TRANSPOSE>
 void launch_batch_blur(const float *in, float *out, const PlanPose *poses, const BlurTile *tiles, int64_t n_tiles,
                        const BlurArgs &b, int grid, cudaStream_t s)
 {
-    const size_t sm = blur_smem_bytes(b.W);
     switch (b.W) {
 #define DFS_BB(WT)                                                                                        \
-    case WT: k_batch_blur<TRANSPOSE, WT><<<grid, kBlurThreads, sm, s>>>(in, out, poses, tiles, n_tiles, b); break;
+    case WT: k_batch_blur<TRANSPOSE, WT><<<grid, kBlurWarps * 32, 0, s>>>(in, out, poses, tiles, n_tiles, b); break;
     DFS_BB(0) DFS_BB(1) DFS_BB(2) DFS_BB(3) DFS_BB(4) DFS_BB(5) DFS_BB(6) DFS_BB(7) DFS_BB(8)
 #undef DFS_BB
-    default: k_batch_blur<TRANSPOSE, -1><<<grid, kBlurThreads, sm, s>>>(in, out, poses, tiles, n_tiles, b); break;
+    default: k_batch_blur<TRANSPOSE, -1><<<grid, kBlurWarps * 32, 0, s>>>(in, out, poses, tiles, n_tiles, b); break;
     }
 }
 
@@ -408,8 +398,7 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
             g += f.n_samples + 1;
             ck += nseg;
         }
-        for (int k0 = 0; k0 < f.n_samples; k0 += kBlurRows)
-            for (int j0 = 0; j0 < f.n_rays; j0 += kBlurRays) tiles[t++] = BlurTile{p, j0, k0, 0};
+        for (int k0 = 0; k0 < f.n_samples; k0 += kBlurRows) tiles[t++] = BlurTile{p, f.n_rays, k0, 0};
         img += (int64_t)f.n_rays * f.n_samples;
     }
     ray0[P] = (int32_t)r;
@@ -420,6 +409,8 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     std::stable_sort(ord.begin(), ord.end(),
                      [&](int32_t x, int32_t y) { return pp[ray_pose[x]].S > pp[ray_pose[y]].S; });
     std::copy(ord.begin(), ord.end(), order);
+    // blur strips of the widest poses first (a strip's work grows with n_rays)
+    std::stable_sort(tiles, tiles + n_tiles, [](const BlurTile &x, const BlurTile &y) { return x.n_rays > y.n_rays; });
 
     BatchLayout L = batch_layout(nullptr, H, vd, prm->blur != 0, prm->speckle != 0);
     if (ws_fwd) *ws_fwd = L.fwd_bytes;
@@ -450,13 +441,10 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     cudaStream_t s = (cudaStream_t)stream;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (trace && cudaStreamIsCapturing(s, &cap) != cudaSuccess) return DIFFUS_E_LAUNCH;
+    // inside a capture an external record becomes an event-record node of the graph
+    const bool external = cap == cudaStreamCaptureStatusActive;
     auto mark = [&](int i) {
-        if (!trace || !trace->event[i]) return;
-        // inside a capture an external record becomes an event-record node of the graph
-        if (cap == cudaStreamCaptureStatusActive)
-            cudaEventRecordWithFlags((cudaEvent_t)trace->event[i], s, cudaEventRecordExternal);
-        else
-            cudaEventRecord((cudaEvent_t)trace->event[i], s);
+        if (trace) record_mark((cudaEvent_t)trace->event[i], external, s);
     };
 
     BatchDev B;
@@ -492,7 +480,7 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     if (rc) return rc;
     mark(DIFFUS_TR_BLUR);
     BlurArgs bl{(float)prm->sigma0, (float)prm->sigma1, H.blurW};
-    const int tgrid = (int)std::min<int64_t>(H.n_tiles, (int64_t)sm_count() * 8);
+    const int tgrid = (int)std::min<int64_t>((H.n_tiles + kBlurWarps - 1) / kBlurWarps, (int64_t)sm_count() * 16);
     const PlanPose *dpose = at<PlanPose>(plan_dev, H.off_pose);
     const BlurTile *dtiles = at<BlurTile>(plan_dev, H.off_tiles);
     if (prm->blur) launch_batch_blur<false>(L.y, images, dpose, dtiles, H.n_tiles, bl, tgrid, s);
@@ -519,9 +507,16 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     const int32_t *ray0 = at<int32_t>(plan_dev, H.off_ray0);
     if (grad_poses) k_pose_reduce_batch<<<(H.P + 3) / 4, 128, 0, s>>>(L.part, ray0, H.P, grad_poses);
     mark(DIFFUS_TR_GATHER);
-    if (grad_vol)
+    if (grad_vol) {
+        GatherMarks gm;
+        if (trace) {
+            gm.units = (cudaEvent_t)trace->event[DIFFUS_TR_GATHER_UNITS];
+            gm.reduce = (cudaEvent_t)trace->event[DIFFUS_TR_GATHER_REDUCE];
+            gm.external = external;
+        }
         rc = launch_gather(vd, L.geo, H.total_rays, H.max_depth, L.gz, (const long long *)B.gz_off, L.gather_ws,
-                           status, grad_vol, H.gather_ctas, s);
+                           status, grad_vol, H.gather_ctas, s, gm);
+    }
     mark(DIFFUS_TR_END);
     return rc ? rc : launch_status();
 }

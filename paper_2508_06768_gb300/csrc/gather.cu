@@ -14,6 +14,12 @@ constexpr int kScanChunk = 4096;
 
 // ------------------------------------------------------------------ runs
 
+// Position inside the box where trilinear sampling needs no clamping.
+__device__ __forceinline__ bool inside(long long X, long long Y, long long Z, const GatherArgs &G)
+{
+    return X >= 0 && (X >> 32) < G.nx - 1 && Y >= 0 && (Y >> 32) < G.ny - 1 && Z >= 0 && (Z >> 32) < G.nz - 1;
+}
+
 __global__ void k_ray_runs(const RayGeo *__restrict__ geo, int n_rays, GatherArgs G, int cap, uint32_t sentinel,
                            Run *__restrict__ runs, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
                            uint32_t *__restrict__ status)
@@ -39,7 +45,18 @@ __global__ void k_ray_runs(const RayGeo *__restrict__ geo, int n_rays, GatherArg
         long long k1 = kn - 1 < S ? kn - 1 : S;
         if (cnt < cap) {
             const uint32_t brick = (uint32_t)((b[2] * G.nby + b[1]) * G.nbx + b[0]);
-            runs[base + cnt] = Run{r, (int)k, (int)k1, (int)brick};
+            Run run;
+            run.X = rg.X0[0] + k * rg.DX[0];
+            run.Y = rg.X0[1] + k * rg.DX[1];
+            run.Z = rg.X0[2] + k * rg.DX[2];
+            run.ray = r;
+            run.k0 = (int)k;
+            run.k1 = (int)k1;
+            // the inner box is convex: the run is clamp-free iff both ends are inside
+            run.clamp = !(inside(run.X, run.Y, run.Z, G) &&
+                          inside(rg.X0[0] + k1 * rg.DX[0], rg.X0[1] + k1 * rg.DX[1], rg.X0[2] + k1 * rg.DX[2], G));
+            run.pad[0] = run.pad[1] = 0;
+            runs[base + cnt] = run;
             keys[base + cnt] = brick;
             vals[base + cnt] = (uint32_t)(base + cnt);
             cnt++;
@@ -387,7 +404,7 @@ static void launch_scan(const uint32_t *in, uint32_t *out, size_t n, uint32_t *s
 
 int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_rays, double max_path_mm,
                   const float *gz, const long long *gz_off, void *ws, uint32_t *status, float *grad_vol,
-                  int ctas_per_sm, cudaStream_t s)
+                  int ctas_per_sm, cudaStream_t s, const GatherMarks &marks)
 {
     const GatherArgs G = make_gather_args(vd);
     const int nb = G.nbx * G.nby * G.nbz;
@@ -417,8 +434,10 @@ int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_r
     k_brick_bounds<<<(unsigned)((slots + 255) / 256), 256, 0, s>>>(L.keys[cur], slots, sentinel, L.bstart, L.bend);
     k_unit_counts<<<(nb + 255) / 256, 256, 0, s>>>(L.bstart, L.bend, nb, L.ucount);
     launch_scan(L.ucount, L.ustart, (size_t)nb, L.sums, L.misc + 0, s);
+    record_mark(marks.units, marks.external, s);
     k_gather_units<<<sms * ctas_per_sm, kGatherWarps * 32, 0, s>>>(geo, gz, gz_off, L.runs, L.vals[cur], L.bstart, L.bend,
                                                          L.ustart, L.misc + 0, nb, G, L.upart);
+    record_mark(marks.reduce, marks.external, s);
     const size_t nv = (size_t)vd->nx * vd->ny * vd->nz;
     k_voxel_reduce<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(L.upart, L.ustart, L.ucount, G, grad_vol);
     return launch_status();

@@ -121,4 +121,27 @@ inline int launch_status()
     return e == cudaSuccess ? DIFFUS_OK : DIFFUS_E_LAUNCH;
 }
 
+// Optional events recorded inside the gradient gather (before the unit
+// gather kernel and after it); `external` marks a stream capture, where the
+// record becomes an event node of the graph.
+struct GatherMarks {
+    cudaEvent_t units = nullptr, reduce = nullptr;
+    bool external = false;
+};
+
+inline void record_mark(cudaEvent_t e, bool external, cudaStream_t s)
+{
+    if (!e) return;
+    if (external)
+        cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, s);
+}
+
+MarchArgs make_march_args(const diffus_volume_desc *vd, const diffus_fan *fan, const diffus_params *prm);
+size_t gather_workspace_bytes(const diffus_volume_desc *vd, long long n_rays, double max_path_mm);
+int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_rays, double max_path_mm,
+                  const float *gz, const long long *gz_off, void *ws, uint32_t *status, float *grad_vol,
+                  int ctas_per_sm, cudaStream_t s, const GatherMarks &marks = GatherMarks());
+
 }  // namespace dfs

@@ -110,9 +110,9 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) k_march_fwd(const T *__restric
 
 // ------------------------------------------------------------------ blur
 
-constexpr int kBlurRows = 32;    // depth rows per tile (one per lane)
-constexpr int kBlurRays = 64;    // output rays per tile
-constexpr int kBlurThreads = 256;
+constexpr int kBlurRows = 32;    // depth rows per strip (one per lane)
+constexpr int kBlurStep = 8;     // rays entering the sliding window per step
+constexpr int kBlurWarps = 4;    // strips (warps) per CTA
 
 struct BlurArgs {
     float sigma0, sigma1;
@@ -128,112 +128,108 @@ __device__ __forceinline__ float blur_w(const BlurArgs &b, int m, int k, float i
     return expf(ex);
 }
 
-// Lateral blur of one pose image (Section 2.4), or its transpose.
-// in/out: [n][S].  Tile: kBlurRays output rays x kBlurRows rows (one row per
-// lane), halo W rays.
+// Lateral blur of one pose image (Section 2.4), or its transpose, on one
+// strip of 32 echo rows [k0, k0 + 32) (one row per lane) across all n rays.
+// in/out: [n][S].
 // Forward:   out[j] = sum_m w_m in[j+m] / N_j        (valid j+m)
 // Transpose: out[j] = sum_m w_m in[j+m] / N_{j+m}    (valid j+m)
-// WT >= 0 is the half-width known at compile time: each warp then keeps a
-// sliding window of 8 + 2W rows in registers and produces 8 output rays from
-// it.  WT < 0 is the general path for wide kernels.
+// with N_j = sum of w_m over the valid j+m.  The warp sweeps the rays once:
+// every input element is read once, kBlurStep rows at a time into a
+// register window of kBlurStep + 2W rows, and every output is written once,
+// each access a coalesced 128-byte row segment.  WT >= 0 is the half-width
+// known at compile time; WT < 0 is the general path for wide kernels, which
+// reads the window through the cache instead.
 template <bool TRANSPOSE, int WT>
-__device__ void blur_tile(const float *__restrict__ in, float *__restrict__ out, int n, int S,
-                          const BlurArgs &b, int j0, int k0, float *sm, float *wsm)
+__device__ void blur_strip(const float *__restrict__ in, float *__restrict__ out, int n, int S,
+                           const BlurArgs &b, int k0)
 {
-    const int W = WT >= 0 ? WT : b.W;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int k = k0 + lane;
+    const bool kin = k < S;
     const float invS = 1.0f / (float)S;
-    const int rows = kBlurRays + 2 * W;
-    for (int m = warp; m <= W; m += nw) wsm[m * 32 + lane] = (k < S) ? blur_w(b, m, k, invS) : 0.0f;
-    if (WT >= 0) {
-        // all of this warp's rows in flight at once (rows is a compile-time bound)
-        constexpr int kRows = kBlurRays + 2 * (WT >= 0 ? WT : 0);
-        constexpr int kPer = (kRows + (kBlurThreads / 32) - 1) / (kBlurThreads / 32);
-        float tmp[kPer];
-#pragma unroll
-        for (int i = 0; i < kPer; i++) {
-            const int rr = warp + i * nw;
-            const int j = j0 - W + rr;
-            tmp[i] = (rr < rows && j >= 0 && j < n && k < S) ? __ldg(in + (size_t)j * S + k) : 0.0f;
-        }
-#pragma unroll
-        for (int i = 0; i < kPer; i++) {
-            const int rr = warp + i * nw;
-            if (rr < rows) sm[rr * 32 + lane] = tmp[i];
-        }
-    } else {
-        for (int rr = warp; rr < rows; rr += nw) {
-            int j = j0 - W + rr;
-            sm[rr * 32 + lane] = (j >= 0 && j < n && k < S) ? in[(size_t)j * S + k] : 0.0f;
-        }
-    }
-    __syncthreads();
-    float full = wsm[lane];
-    for (int m = 1; m <= W; m++) full += 2.0f * wsm[m * 32 + lane];
-    auto norm_of = [&](int j) -> float {
-        if (j >= W && j < n - W) return full;
-        float N = 0.0f;
-        for (int m = -W; m <= W; m++)
-            if (j + m >= 0 && j + m < n) N += wsm[(m < 0 ? -m : m) * 32 + lane];
-        return N;
-    };
-    if (TRANSPOSE) {
-        for (int rr = warp; rr < rows; rr += nw) {
-            int j = j0 - W + rr;
-            if (j < 0 || j >= n) continue;
-            sm[rr * 32 + lane] *= 1.0f / norm_of(j);
-        }
-        __syncthreads();
-    }
+    const float *src = in + (kin ? k : 0);
+    float *dst = out + (kin ? k : 0);
     if (WT >= 0) {
         constexpr int WW = WT >= 0 ? WT : 0;
-        constexpr int RPW = kBlurRays / 8;                 // output rays per warp (8 warps)
+        constexpr int B = kBlurStep;
         float w[WW + 1];
 #pragma unroll
-        for (int m = 0; m <= WW; m++) w[m] = wsm[m * 32 + lane];
-        for (int g = warp; g < kBlurRays / RPW; g += nw) {
-            float win[RPW + 2 * WW];
+        for (int m = 0; m <= WW; m++) w[m] = kin ? blur_w(b, m, k, invS) : (m == 0 ? 1.0f : 0.0f);
+        float full = w[0];
 #pragma unroll
-            for (int t = 0; t < RPW + 2 * WW; t++) win[t] = sm[(g * RPW + t) * 32 + lane];
+        for (int m = 1; m <= WW; m++) full += 2.0f * w[m];
+        const float rfull = 1.0f / full;
+        auto rnorm = [&](int j) -> float {          // 1 / N_j
+            if (j >= WW && j < n - WW) return rfull;
+            float N = 0.0f;
 #pragma unroll
-            for (int i = 0; i < RPW; i++) {
-                const int j = j0 + g * RPW + i;
+            for (int m = -WW; m <= WW; m++)
+                if (j + m >= 0 && j + m < n) N += w[m < 0 ? -m : m];
+            return 1.0f / N;
+        };
+        auto ld = [&](int j) -> float {
+            if (!kin || j < 0 || j >= n) return 0.0f;
+            float x = __ldg(src + (size_t)j * S);
+            if (TRANSPOSE) x *= rnorm(j);
+            return x;
+        };
+        float win[B + 2 * WW];
+#pragma unroll
+        for (int t = 0; t < 2 * WW; t++) win[t] = ld(t - WW);
+        for (int jb = 0; jb < n; jb += B) {
+            float nx[B];
+#pragma unroll
+            for (int t = 0; t < B; t++) nx[t] = (kin && jb + WW + t < n) ? __ldg(src + (size_t)(jb + WW + t) * S) : 0.0f;
+#pragma unroll
+            for (int t = 0; t < B; t++)
+                win[2 * WW + t] = (TRANSPOSE && jb + WW + t < n) ? nx[t] * rnorm(jb + WW + t) : nx[t];
+#pragma unroll
+            for (int i = 0; i < B; i++) {
+                const int j = jb + i;
                 float acc = w[0] * win[i + WW];
 #pragma unroll
                 for (int m = 1; m <= WW; m++) acc = fmaf(w[m], win[i + WW - m] + win[i + WW + m], acc);
-                if (j < n && k < S) {
-                    if (!TRANSPOSE) acc *= 1.0f / norm_of(j);
-                    out[(size_t)j * S + k] = acc;
+                if (kin && j < n) {
+                    if (!TRANSPOSE) acc *= rnorm(j);
+                    dst[(size_t)j * S] = acc;
                 }
             }
+#pragma unroll
+            for (int t = 0; t < 2 * WW; t++) win[t] = win[t + B];
         }
         return;
     }
-    for (int oj = warp; oj < kBlurRays; oj += nw) {
-        int j = j0 + oj;
-        if (j >= n || k >= S) continue;
-        float acc = 0.0f;
-        const float *col = sm + (oj + W) * 32 + lane;
-        for (int m = -W; m <= W; m++) acc = fmaf(wsm[(m < 0 ? -m : m) * 32 + lane], col[m * 32], acc);
-        if (!TRANSPOSE) acc *= 1.0f / norm_of(j);
-        out[(size_t)j * S + k] = acc;
+    if (!kin) return;
+    const int W = b.W;
+    auto wt = [&](int m) { return blur_w(b, m < 0 ? -m : m, k, invS); };
+    auto N_of = [&](int j) {
+        float N = 0.0f;
+        for (int m = -W; m <= W; m++)
+            if (j + m >= 0 && j + m < n) N += wt(m);
+        return N;
+    };
+    auto ld = [&](int j) -> float {
+        if (j < 0 || j >= n) return 0.0f;
+        float x = __ldg(src + (size_t)j * S);
+        if (TRANSPOSE) x *= 1.0f / N_of(j);
+        return x;
+    };
+    for (int j = 0; j < n; j++) {
+        float acc = wt(0) * ld(j);
+        for (int m = 1; m <= W; m++) acc = fmaf(wt(m), ld(j - m) + ld(j + m), acc);
+        if (!TRANSPOSE) acc *= 1.0f / N_of(j);
+        dst[(size_t)j * S] = acc;
     }
 }
 
+// Single-pose blur: one warp per strip.
 template <bool TRANSPOSE, int WT>
-__global__ void __launch_bounds__(kBlurThreads) k_blur(const float *__restrict__ in, float *__restrict__ out,
-                                                       int n, int S, BlurArgs b)
+__global__ void __launch_bounds__(kBlurWarps * 32) k_blur(const float *__restrict__ in, float *__restrict__ out,
+                                                          int n, int S, BlurArgs b)
 {
-    extern __shared__ float dyn[];
-    float *wsm = dyn;                       // (kMaxW + 1) x 32
-    float *sm = dyn + (kMaxW + 1) * 32;     // (kBlurRays + 2W) x 32
-    int j0 = blockIdx.y * kBlurRays;
-    int k0 = blockIdx.x * kBlurRows;
-    blur_tile<TRANSPOSE, WT>(in, out, n, S, b, j0, k0, sm, wsm);
+    const int strip = blockIdx.x * kBlurWarps + (threadIdx.x >> 5);
+    if (strip * kBlurRows >= S) return;
+    blur_strip<TRANSPOSE, WT>(in, out, n, S, b, strip * kBlurRows);
 }
-
-inline size_t blur_smem_bytes(int W) { return sizeof(float) * 32 * ((kMaxW + 1) + kBlurRays + 2 * W); }
 
 }  // namespace dfs

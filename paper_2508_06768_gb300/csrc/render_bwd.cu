@@ -8,13 +8,8 @@ using namespace dfs;
 namespace dfs {
 
 int launch_blur(const float *in, float *out, int n, int S, const diffus_params *prm, bool transpose, cudaStream_t s);
-size_t gather_workspace_bytes(const diffus_volume_desc *vd, long long n_rays, double max_path_mm);
-int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_rays, double max_path_mm,
-                  const float *gz, const long long *gz_off, void *ws, uint32_t *status, float *grad_vol,
-                  int ctas_per_sm, cudaStream_t s);
 int check_common(const void *vol, const diffus_volume_desc *vd, const float *pose, const diffus_fan *fan,
                  const diffus_params *prm);
-MarchArgs make_march_args(const diffus_volume_desc *vd, const diffus_fan *fan, const diffus_params *prm);
 
 constexpr int kWarpsBwd = 4;
 

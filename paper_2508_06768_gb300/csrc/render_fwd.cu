@@ -77,13 +77,13 @@ int launch_blur(const float *in, float *out, int n, int S, const diffus_params *
                 cudaStream_t s)
 {
     BlurArgs b{(float)prm->sigma0, (float)prm->sigma1, blur_halfwidth(prm)};
-    dim3 grid((S + kBlurRows - 1) / kBlurRows, (n + kBlurRays - 1) / kBlurRays);
-    size_t sm = blur_smem_bytes(b.W);
-#define DFS_BLUR(WT)                                                                  \
-    if (transpose)                                                                    \
-        k_blur<true, WT><<<grid, kBlurThreads, sm, s>>>(in, out, n, S, b);            \
-    else                                                                              \
-        k_blur<false, WT><<<grid, kBlurThreads, sm, s>>>(in, out, n, S, b);
+    const int strips = (S + kBlurRows - 1) / kBlurRows;
+    const int grid = (strips + kBlurWarps - 1) / kBlurWarps;
+#define DFS_BLUR(WT)                                                        \
+    if (transpose)                                                          \
+        k_blur<true, WT><<<grid, kBlurWarps * 32, 0, s>>>(in, out, n, S, b); \
+    else                                                                    \
+        k_blur<false, WT><<<grid, kBlurWarps * 32, 0, s>>>(in, out, n, S, b);
     switch (b.W) {
     case 0: DFS_BLUR(0) break;
     case 1: DFS_BLUR(1) break;
