@@ -105,8 +105,12 @@ typedef struct {
  *    mean over rays j-W..j+W inside the fan with weights
  *    exp(-m^2 / (2 s_k^2)), s_k = sigma0 + sigma1 (k+1)/S (in rays),
  *    W = ceil(3 (sigma0 + sigma1)) <= 32.
- *  refine: BF16 volumes only - one refinement pass of the per-ray depth
- *    recurrence with the residual computed in FP64 (batched path). */
+ *  refine: 1 adds one iterative-refinement pass to the forward solve of
+ *    Eq. 2-4: the residuals of the FP32 depth recurrence are computed in
+ *    FP64 (coefficients recomputed in FP64 from the same samples), the
+ *    error recurrence is solved in FP32 and the echoes use the corrected
+ *    states.  Any volume dtype, single-pose and batched forward; the
+ *    adjoint stays FP32. */
 typedef struct {
     uint64_t seed;
     int32_t mode;

@@ -28,6 +28,7 @@ struct PlanPose {
     float a2;
     int32_t W;
     int64_t img_off;
+    double a2d;
 };
 
 struct BlurTile {                 // one 32-row strip of one pose image
@@ -153,7 +154,7 @@ __global__ void k_batch_setup(const float *__restrict__ poses, BatchDev B, VolPl
 }
 
 // Persistent forward: each warp takes rays from the queue (longest first).
-template <typename T, int WARPS>
+template <typename T, int WARPS, bool REFINE>
 __global__ void __launch_bounds__(WARPS * 32) k_batch_fwd(const T *__restrict__ vol, MarchArgs A, BatchDev B,
                                                           const RayGeo *__restrict__ geo, float *__restrict__ out,
                                                           int *__restrict__ valid, uint32_t *__restrict__ status,
@@ -161,6 +162,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch_fwd(const T *__restrict__ 
                                                           float *__restrict__ mbuf)
 {
     __shared__ float buf[WARPS][kSegPad];
+    __shared__ double dbuf[REFINE ? WARPS : 1][REFINE ? kSegPad : 1];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
         unsigned q = 0;
@@ -171,9 +173,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch_fwd(const T *__restrict__ 
         RayGeo rg = geo[r];
         MarchArgs Ap = A;
         Ap.a2 = B.pose[rg.pose].a2;
+        Ap.a2d = B.pose[rg.pose].a2d;
         RayOut o{out + B.row_off[r], valid ? valid + r : nullptr, status, ckpt ? ckpt + B.ck_off[r] : nullptr,
                  mbuf ? mbuf + B.row_off[r] : nullptr};
-        march_fwd_ray<T>(vol, Ap, rg, o, buf[w]);
+        march_fwd_ray<T, REFINE>(vol, Ap, rg, o, buf[w], REFINE ? dbuf[w] : nullptr);
         __syncwarp();
     }
 }
@@ -197,6 +200,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch_bwd(const T *__restrict__ 
         RayGeo rg = geo[r];
         MarchArgs Ap = A;
         Ap.a2 = B.pose[rg.pose].a2;
+        Ap.a2d = B.pose[rg.pose].a2d;
         march_bwd_ray<T>(vol, Ap, rg, gy + B.row_off[r], gz + B.gz_off[r], part + 6 * (size_t)r,
                          ckpt + B.ck_off[r], sm[w], true, mbuf ? mbuf + B.row_off[r] : nullptr);
         __syncwarp();
@@ -240,10 +244,15 @@ int sm_count()
 
 template <typename T, int WARPS>
 void launch_fwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out, int *valid,
-                  uint32_t *status, unsigned *counter, float4 *ckpt, float *mbuf, int grid, cudaStream_t s)
+                  uint32_t *status, unsigned *counter, float4 *ckpt, float *mbuf, int grid, bool refine,
+                  cudaStream_t s)
 {
-    k_batch_fwd<T, WARPS><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status, counter, ckpt,
-                                                      mbuf);
+    if (refine)
+        k_batch_fwd<T, WARPS, true><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status,
+                                                                counter, ckpt, mbuf);
+    else
+        k_batch_fwd<T, WARPS, false><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status,
+                                                                 counter, ckpt, mbuf);
 }
 
 template <typename T, int WARPS>
@@ -256,12 +265,13 @@ void launch_bwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const 
 
 template <typename T>
 int launch_fwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out,
-                 int *valid, uint32_t *status, unsigned *counter, float4 *ckpt, float *mbuf, int grid, cudaStream_t s)
+                 int *valid, uint32_t *status, unsigned *counter, float4 *ckpt, float *mbuf, int grid, bool refine,
+                 cudaStream_t s)
 {
     switch (warps) {
-    case 2: launch_fwd_t<T, 2>(vol, A, B, geo, out, valid, status, counter, ckpt, mbuf, grid, s); break;
-    case 4: launch_fwd_t<T, 4>(vol, A, B, geo, out, valid, status, counter, ckpt, mbuf, grid, s); break;
-    case 8: launch_fwd_t<T, 8>(vol, A, B, geo, out, valid, status, counter, ckpt, mbuf, grid, s); break;
+    case 2: launch_fwd_t<T, 2>(vol, A, B, geo, out, valid, status, counter, ckpt, mbuf, grid, refine, s); break;
+    case 4: launch_fwd_t<T, 4>(vol, A, B, geo, out, valid, status, counter, ckpt, mbuf, grid, refine, s); break;
+    case 8: launch_fwd_t<T, 8>(vol, A, B, geo, out, valid, status, counter, ckpt, mbuf, grid, refine, s); break;
     default: return DIFFUS_E_PLAN;
     }
     return DIFFUS_OK;
@@ -384,7 +394,7 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     for (int p = 0; p < P; p++) {
         const diffus_fan &f = fans[p];
         double a = attenuation_a(&f);
-        pp[p] = PlanPose{f.n_rays, f.n_samples, f.fov_rad, f.depth_mm, (float)(a * a), H.blurW, img};
+        pp[p] = PlanPose{f.n_rays, f.n_samples, f.fov_rad, f.depth_mm, (float)(a * a), H.blurW, img, a * a};
         depth[p] = f.depth_mm;
         ray0[p] = (int32_t)r;
         img_offsets[p] = img;
@@ -473,10 +483,10 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     float *mb = bwd ? L.mbuf : nullptr;
     if (vd->dtype == DIFFUS_F32)
         rc = launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0, ck, mb, grid,
-                                 s);
+                                 prm->refine != 0, s);
     else
         rc = launch_fwd_w<unsigned short>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0,
-                                          ck, mb, grid, s);
+                                          ck, mb, grid, prm->refine != 0, s);
     if (rc) return rc;
     mark(DIFFUS_TR_BLUR);
     BlurArgs bl{(float)prm->sigma0, (float)prm->sigma1, H.blurW};

@@ -159,6 +159,37 @@ __device__ __forceinline__ Xfer xfer(float r, float a2, int mode)
     return t;
 }
 
+// FP64 interface coefficient and transfer entries, recomputed from the
+// same FP32 sample pairs for the residual of the refinement pass.
+__device__ __forceinline__ double refl64(float zr1, float dz1, float zr2, float dz2)
+{
+    const double dZ = ((double)zr2 - (double)zr1) + ((double)dz2 - (double)dz1);
+    const double sZ = ((double)zr1 + (double)dz1) + ((double)zr2 + (double)dz2);
+    return dZ / sZ;
+}
+
+struct Xfer64 {
+    double m00, m01, m10, delta;
+};
+
+__device__ __forceinline__ Xfer64 xfer64(double r, double a2, int mode)
+{
+    Xfer64 t;
+    const double r2 = r * r;
+    if (mode == DIFFUS_MODE_LITERAL) {
+        const double R = fabs(r);
+        t.m00 = a2 * fma(-2.0, r2, 1.0);
+        t.m01 = a2 * R;
+        t.m10 = -R;
+    } else {
+        t.m00 = a2;
+        t.m01 = a2 * r;
+        t.m10 = r;
+    }
+    t.delta = a2 * (1.0 - r2);
+    return t;
+}
+
 struct Mat2 {
     float a, b, c, d;   // [[a, b], [c, d]]
 };

@@ -93,19 +93,20 @@ static __global__ void k_ray_setup(const float *__restrict__ pose6, FanDev fan, 
 // One warp per ray, kWarpsFwd warps per CTA.
 constexpr int kWarpsFwd = 4;
 
-template <typename T>
+template <typename T, bool REFINE>
 __global__ void __launch_bounds__(kWarpsFwd * 32) k_march_fwd(const T *__restrict__ vol, MarchArgs A,
                                                               const RayGeo *__restrict__ geo, int n_rays,
                                                               float *__restrict__ out, int *__restrict__ valid,
                                                               uint32_t *__restrict__ status)
 {
     __shared__ float buf[kWarpsFwd][kSegPad];
+    __shared__ double dbuf[REFINE ? kWarpsFwd : 1][REFINE ? kSegPad : 1];
     const int w = threadIdx.x >> 5;
     const int j = blockIdx.x * kWarpsFwd + w;
     if (j >= n_rays) return;
     RayGeo rg = geo[j];
     RayOut o{out + (size_t)j * rg.S, valid ? valid + j : nullptr, status, nullptr, nullptr};
-    march_fwd_ray<T>(vol, A, rg, o, buf[w]);
+    march_fwd_ray<T, REFINE>(vol, A, rg, o, buf[w], REFINE ? dbuf[w] : nullptr);
 }
 
 // ------------------------------------------------------------------ blur

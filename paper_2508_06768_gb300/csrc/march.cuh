@@ -25,6 +25,7 @@ struct MarchArgs {
     VolGeo g;
     float a2;         // a^2, round-trip amplitude factor of one cell
     int mode;
+    double a2d;       // a^2 in FP64 (residual of the refinement pass)
     Speckle sp;
 };
 
@@ -48,9 +49,10 @@ __device__ __forceinline__ void sample_pos(const RayGeo &rg, int k, long long &X
 // Phase A of a segment: samples base+1 .. base+256 lane-interleaved and
 // writes r_i (i = base..base+255, 0 past the ray) into buf[smem_idx(i-base)].
 // (czr, cdz) carries the sample at `base` in and the one at base+256 out.
-template <typename T>
+template <typename T, bool REFINE = false>
 __device__ __forceinline__ void seg_reflections(const T *__restrict__ vol, const VolGeo &g, const RayGeo &rg,
-                                                int base, float &czr, float &cdz, float *__restrict__ buf)
+                                                int base, float &czr, float &cdz, float *__restrict__ buf,
+                                                double *__restrict__ dbuf = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int S = rg.S;
@@ -71,6 +73,7 @@ __device__ __forceinline__ void seg_reflections(const T *__restrict__ vol, const
         if (lane == 0) { lzr = pzr; ldz = pdz; }
         float r = (k - 1 < S) ? refl(lzr, ldz, zr, dz) : 0.0f;
         buf[smem_idx(t * kWarp + lane)] = r;
+        if (REFINE) dbuf[smem_idx(t * kWarp + lane)] = (k - 1 < S) ? refl64(lzr, ldz, zr, dz) : 0.0;
         pzr = __shfl_sync(0xffffffffu, zr, 31);
         pdz = __shfl_sync(0xffffffffu, dz, 31);
     }
@@ -116,6 +119,43 @@ __device__ __forceinline__ void warp_scan_prefix(Mat2 Q, float dq, Mat2 &E, floa
     }
     Qall = shfl_mat(Q, 31);
     dall = __shfl_sync(0xffffffffu, dq, 31);
+}
+
+// Warp scan of the affine maps e -> e Q + c (row vector e = (e0, e1), with
+// the determinant part eD -> eD dq + cD) of the refinement pass: returns the
+// exclusive prefix offsets (c0, c1, cD) of this lane (the matrix part is the
+// prefix E of warp_scan_prefix) and the segment total offsets (t0, t1, tD).
+__device__ __forceinline__ void warp_scan_affine(Mat2 Q, float dq, float &c0, float &c1, float &cD, float &t0,
+                                                 float &t1, float &tD)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < kWarp; off <<= 1) {
+        Mat2 P = shfl_up_mat(Q, off);
+        float pd = __shfl_up_sync(0xffffffffu, dq, off);
+        float p0 = __shfl_up_sync(0xffffffffu, c0, off);
+        float p1 = __shfl_up_sync(0xffffffffu, c1, off);
+        float pD = __shfl_up_sync(0xffffffffu, cD, off);
+        if (lane >= off) {
+            // earlier lanes first: e (P Q) + (p Q + c)
+            const float n0 = fmaf(p0, Q.a, fmaf(p1, Q.c, c0));
+            const float n1 = fmaf(p0, Q.b, fmaf(p1, Q.d, c1));
+            cD = fmaf(pD, dq, cD);
+            c0 = n0;
+            c1 = n1;
+            Q = mat_mul(P, Q);
+            dq = pd * dq;
+        }
+    }
+    t0 = __shfl_sync(0xffffffffu, c0, 31);
+    t1 = __shfl_sync(0xffffffffu, c1, 31);
+    tD = __shfl_sync(0xffffffffu, cD, 31);
+    float x0 = __shfl_up_sync(0xffffffffu, c0, 1);
+    float x1 = __shfl_up_sync(0xffffffffu, c1, 1);
+    float xD = __shfl_up_sync(0xffffffffu, cD, 1);
+    c0 = lane ? x0 : 0.0f;
+    c1 = lane ? x1 : 0.0f;
+    cD = lane ? xD : 0.0f;
 }
 
 // Radial white normals of group q (4 rows 4q..4q+3), stream 0.
@@ -181,10 +221,18 @@ __device__ __forceinline__ void chunk_speckle(const Speckle &sp, int i0, int S, 
 }
 
 // Forward march of one ray by one warp.  buf: this warp's shared row of
-// kSegPad floats.
-template <typename T>
+// kSegPad floats; dbuf: kSegPad doubles when REFINE.
+//
+// REFINE adds one iterative-refinement pass of the depth recurrence
+// b_{i+1} = b_i M_i, D_{i+1} = D_i delta_i per segment: the FP32 states are
+// kept, their residuals rho_{i+1} = b_i M_i - b_{i+1} are computed in FP64
+// with M_i recomputed in FP64 from the same samples, the error recurrence
+// e_{i+1} = e_i M_i + rho_{i+1} (e_0 = 0) of e_i = b*_i - b_i (b* the states
+// of the FP64 coefficients) is solved in FP32 with the same scan (affine
+// maps), and the echoes use the corrected states b_i + e_i.
+template <typename T, bool REFINE = false>
 __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, const RayGeo &rg,
-                              const RayOut &out, float *__restrict__ buf)
+                              const RayOut &out, float *__restrict__ buf, double *__restrict__ dbuf = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int S = rg.S;
@@ -197,9 +245,11 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
     int nonfinite = 0;
     const bool vec4 = ((((uintptr_t)out.row) & 15) == 0);
 
+    float es0 = 0.0f, es1 = 0.0f, esD = 0.0f;  // refinement: correction at segment start
+
     for (int base = 0; base < S; base += kSeg) {
-        if (out.ckpt && lane == 0) out.ckpt[base / kSeg] = make_float4(bs0, bs1, Ds, 0.0f);
-        seg_reflections<T>(vol, A.g, rg, base, czr, cdz, buf);
+        if (out.ckpt && lane == 0) out.ckpt[base / kSeg] = make_float4(bs0 + es0, bs1 + es1, Ds + esD, 0.0f);
+        seg_reflections<T, REFINE>(vol, A.g, rg, base, czr, cdz, buf, dbuf);
         __syncwarp();
         const int i0 = base + lane * kChunk;
         float rr[kChunk];
@@ -232,21 +282,109 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                 if (i0 + t < S) out.mrow[i0 + t] = m[t];
         }
         float y[kChunk];
+        if (!REFINE) {
 #pragma unroll
-        for (int t = 0; t < kChunk; t++) {
-            const int i = i0 + t;
-            y[t] = 0.0f;
-            if (i < S) {
-                Xfer x = xfer(rr[t], A.a2, A.mode);
-                float q = fmaf(b0, x.m01, b1);          // det(A_{i+1})
-                float e = x.m01 * D * frcp(b1 * q);
-                if (!(q >= kPoleEps)) first_bad = min(first_bad, i + 1);
-                float nb0 = fmaf(b0, x.m00, b1 * x.m10);
-                b1 = q;
-                b0 = nb0;
-                D *= x.delta;
-                y[t] = m[t] * e;
-                nonfinite += !isfinite(y[t]);
+            for (int t = 0; t < kChunk; t++) {
+                const int i = i0 + t;
+                y[t] = 0.0f;
+                if (i < S) {
+                    Xfer x = xfer(rr[t], A.a2, A.mode);
+                    float q = fmaf(b0, x.m01, b1);          // det(A_{i+1})
+                    float e = x.m01 * D * frcp(b1 * q);
+                    if (!(q >= kPoleEps)) first_bad = min(first_bad, i + 1);
+                    float nb0 = fmaf(b0, x.m00, b1 * x.m10);
+                    b1 = q;
+                    b0 = nb0;
+                    D *= x.delta;
+                    y[t] = m[t] * e;
+                    nonfinite += !isfinite(y[t]);
+                }
+            }
+        } else {
+            // FP32 states b_i, D_i of the chunk as the unrefined path computes them
+            float sb0[kChunk + 1], sb1[kChunk + 1], sD[kChunk + 1];
+            sb0[0] = b0;
+            sb1[0] = b1;
+            sD[0] = D;
+#pragma unroll
+            for (int t = 0; t < kChunk; t++) {
+                sb0[t + 1] = sb0[t];
+                sb1[t + 1] = sb1[t];
+                sD[t + 1] = sD[t];
+                if (i0 + t < S) {
+                    Xfer x = xfer(rr[t], A.a2, A.mode);
+                    sb0[t + 1] = fmaf(sb0[t], x.m00, sb1[t] * x.m10);
+                    sb1[t + 1] = fmaf(sb0[t], x.m01, sb1[t]);
+                    sD[t + 1] = sD[t] * x.delta;
+                }
+            }
+            // the state after the chunk is the next lane's start (the next
+            // segment's carry for lane 31)
+            {
+                float n0 = __shfl_down_sync(0xffffffffu, b0, 1);
+                float n1 = __shfl_down_sync(0xffffffffu, b1, 1);
+                float nD = __shfl_down_sync(0xffffffffu, D, 1);
+                if (lane == 31) {
+                    n0 = bs0;
+                    n1 = bs1;
+                    nD = Ds;
+                }
+                if (i0 + kChunk <= S) {
+                    sb0[kChunk] = n0;
+                    sb1[kChunk] = n1;
+                    sD[kChunk] = nD;
+                }
+            }
+            // FP64 residuals and the chunk's local correction map e -> e Q + c
+            float rho0[kChunk], rho1[kChunk], rhoD[kChunk];
+            float c0 = 0.0f, c1 = 0.0f, cD = 0.0f;
+#pragma unroll
+            for (int t = 0; t < kChunk; t++) {
+                rho0[t] = rho1[t] = rhoD[t] = 0.0f;
+                if (i0 + t < S) {
+                    const Xfer64 x = xfer64(dbuf[smem_idx(lane * kChunk + t)], A.a2d, A.mode);
+                    const double p0 = sb0[t], p1 = sb1[t];
+                    // rho = b_i M_i - b_{i+1}: what the FP32 step lost
+                    rho0[t] = (float)(fma(p0, x.m00, p1 * x.m10) - (double)sb0[t + 1]);
+                    rho1[t] = (float)(fma(p0, x.m01, p1) - (double)sb1[t + 1]);
+                    rhoD[t] = (float)((double)sD[t] * x.delta - (double)sD[t + 1]);
+                    const Xfer xf = xfer(rr[t], A.a2, A.mode);
+                    const float n0 = fmaf(c0, xf.m00, fmaf(c1, xf.m10, rho0[t]));
+                    c1 = fmaf(c0, xf.m01, c1 + rho1[t]);
+                    c0 = n0;
+                    cD = fmaf(cD, xf.delta, rhoD[t]);
+                }
+            }
+            float t0, t1, tD;
+            warp_scan_affine(Q, dq, c0, c1, cD, t0, t1, tD);
+            // correction at this lane's chunk start, and the next segment's
+            float e0 = fmaf(es0, E.a, fmaf(es1, E.c, c0));
+            float e1 = fmaf(es0, E.b, fmaf(es1, E.d, c1));
+            float eD = fmaf(esD, de, cD);
+            {
+                const float n0 = fmaf(es0, Qall.a, fmaf(es1, Qall.c, t0));
+                const float n1 = fmaf(es0, Qall.b, fmaf(es1, Qall.d, t1));
+                esD = fmaf(esD, dall, tD);
+                es0 = n0;
+                es1 = n1;
+            }
+#pragma unroll
+            for (int t = 0; t < kChunk; t++) {
+                const int i = i0 + t;
+                y[t] = 0.0f;
+                if (i < S) {
+                    const Xfer x = xfer(rr[t], A.a2, A.mode);
+                    const float cb1 = sb1[t] + e1, cDv = sD[t] + eD;   // corrected b1_i, D_i
+                    const float n0 = fmaf(e0, x.m00, fmaf(e1, x.m10, rho0[t]));
+                    e1 = fmaf(e0, x.m01, e1 + rho1[t]);
+                    e0 = n0;
+                    eD = fmaf(eD, x.delta, rhoD[t]);
+                    const float q = sb1[t + 1] + e1;                   // corrected det(A_{i+1})
+                    const float e = x.m01 * cDv * frcp(cb1 * q);
+                    if (!(q >= kPoleEps)) first_bad = min(first_bad, i + 1);
+                    y[t] = m[t] * e;
+                    nonfinite += !isfinite(y[t]);
+                }
             }
         }
         if (vec4 && i0 + kChunk <= S) {

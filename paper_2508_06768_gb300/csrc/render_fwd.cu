@@ -36,6 +36,7 @@ MarchArgs make_march_args(const diffus_volume_desc *vd, const diffus_fan *fan, c
     A.g = make_volgeo(vd);
     double a = attenuation_a(fan);
     A.a2 = (float)(a * a);
+    A.a2d = a * a;
     A.mode = prm->mode;
     A.sp = make_speckle(prm);
     return A;
@@ -64,12 +65,14 @@ int launch_fwd_march(const void *vol, const diffus_volume_desc *vd, const float 
     k_ray_setup<<<(fan->n_rays + 127) / 128, 128, 0, s>>>(pose, fd, make_place(vd), geo);
     MarchArgs A = make_march_args(vd, fan, prm);
     int grid = (fan->n_rays + kWarpsFwd - 1) / kWarpsFwd;
-    if (vd->dtype == DIFFUS_F32)
-        k_march_fwd<float><<<grid, kWarpsFwd * 32, 0, s>>>((const float *)vol, A, geo, fan->n_rays, out,
-                                                           ray_valid, status);
-    else
-        k_march_fwd<unsigned short><<<grid, kWarpsFwd * 32, 0, s>>>((const unsigned short *)vol, A, geo,
-                                                                    fan->n_rays, out, ray_valid, status);
+#define DFS_FWD(T, R) \
+    k_march_fwd<T, R><<<grid, kWarpsFwd * 32, 0, s>>>((const T *)vol, A, geo, fan->n_rays, out, ray_valid, status)
+    if (vd->dtype == DIFFUS_F32) {
+        if (prm->refine) DFS_FWD(float, true); else DFS_FWD(float, false);
+    } else {
+        if (prm->refine) DFS_FWD(unsigned short, true); else DFS_FWD(unsigned short, false);
+    }
+#undef DFS_FWD
     return launch_status();
 }
 
