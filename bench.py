@@ -68,10 +68,13 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0:   # sampling has started
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
@@ -133,7 +136,7 @@ BOUND = {"march_fwd": "alu", "march_bwd": "alu", "gather_units": "alu", "blur": 
 # DRAM bytes per ray-sample measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch over the 64-pose prefix of the
 # workload, divided by its ray-samples); absent where the kernel changed since.
-NCU_DRAM_PER_UNIT = {}
+NCU_DRAM_PER_UNIT = {"march_fwd": 6.29, "blur": 6.02, "blur_T": 6.03, "march_bwd": 11.82}
 
 
 def median_pose_order(fans):
@@ -329,6 +332,36 @@ def run_forms(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, stream,
                                     "per-pose volume gradients are not summed"}
     del g
     out["speedup_fwd_vs_plain"] = out["plain_fwd"]["ms"] / fwd_ms
+    del img, gv, wsp
+    out.update(run_scale_form(torch, flush, stream, steps, warmup))
+    return out
+
+
+def run_scale_form(torch, flush, stream, steps, warmup):
+    """Precision + scale workload: 512^3 BF16 volume at 0.5 mm, 64 hemisphere
+    poses x 1024 rays x 4096 samples at 0.05 mm, 7 MHz, forward+backward,
+    with and without the FP64-residual refinement pass."""
+    from paper_2508_06768_gb300.render import BatchRenderer
+    dev = torch.device("cuda", torch.cuda.current_device())
+    v5 = I.fine_brain_phantom(512, 0.5, seed=5)
+    poses5 = torch.from_numpy(I.hemisphere_poses(v5, 64, seed=5)).to(dev)
+    fans5 = [I.Fan(1024, 4096, math.radians(60.0), 4096 * 0.05, 7.0, 0.5) for _ in range(64)]
+    total5 = sum(f.n_rays * f.n_samples for f in fans5)
+    vb = torch.from_numpy(v5.data).to(dev).to(torch.bfloat16)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(55)
+    G5 = torch.randn(total5, generator=gen, device=dev, dtype=torch.float32)
+    out = {}
+    for refine in (1, 0):
+        prm5 = I.Params(seed=5, mode=0, refine=refine)
+        r5 = BatchRenderer(vb, v5.spacing, v5.origin, fans5, prm5, with_bwd=True)
+        g = _capture(torch, lambda s: r5.run(poses5, G5, stream=s))
+        ms = _time_graph(torch, g, flush, stream, max(1, min(steps, 5)), warmup)
+        key = "scale_bf16_fwd_bwd_refine" if refine else "scale_bf16_fwd_bwd"
+        out[key] = {"value": total5 / (ms * 1e-3), "ms": ms, "ray_samples": total5,
+                    "workload": "512^3 BF16 at 0.5 mm, 64 poses x 1024 rays x 4096 samples at 0.05 mm, 7 MHz, "
+                                "literal |R|, speckle+blur%s" % (", FP64-residual refinement" if refine else "")}
+        del g, r5
     return out
 
 
@@ -370,6 +403,8 @@ def run_native(args):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    # clocks are sampled from the warm-up to the end of the end-to-end leg
+    clk = ClockSampler(local).__enter__()
     for _ in range(args.warmup):
         flush.zero_()
         graph.replay()
@@ -380,16 +415,15 @@ def run_native(args):
         dist.barrier()
     torch.cuda.synchronize()
     total_ms = 0.0
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
-            e0.record(stream)
-            graph.replay()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            total_ms += e0.elapsed_time(e1)
-            for k, (a, b) in TRACE.items():
-                kern_ms[k] += events[a].elapsed_time(events[b])
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        for k, (a, b) in TRACE.items():
+            kern_ms[k] += events[a].elapsed_time(events[b])
     torch.cuda.synchronize()
     if ws > 1:
         t = torch.tensor([total_ms], device=dev)
@@ -400,7 +434,6 @@ def run_native(args):
     value = total * ws / (ms_per_step * 1e-3)
     kern_ms = {k: v / args.steps for k, v in kern_ms.items()}
     status = r.status.cpu().numpy().view(np.uint32)
-    clocks = clk.summary()
     images_h = r.images.cpu().numpy()
     gposes_h = r.grad_poses.cpu().numpy()
 
@@ -434,6 +467,8 @@ def run_native(args):
         e2e_ms = tt / n_e2e
         e2e = {"value": total * ws / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
+    clk.__exit__(None, None, None)
+    clocks = clk.summary()
 
     # ---- forms: batched vs the plain single-pose kernel, forward only, speckle off, BF16
     forms = None

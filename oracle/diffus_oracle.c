@@ -684,7 +684,8 @@ int or_render(const float *vol, const or_grid *g, const double pose[6], const or
 
 /* Gradient of L = sum(gimg * img) for one pose with respect to the volume
  * (gvol, accumulated, may be NULL) and the six pose parameters (gpose,
- * overwritten).  All rays are used. */
+ * overwritten).  A ray whose adjoint row (after the blur transpose) is all
+ * zero contributes exactly zero and is skipped. */
 int or_render_grad(const float *vol, const or_grid *g, const double pose[6], const or_fan *fan,
                    const or_params *p, uint32_t pose_ctr, const double *gimg, double *gvol, double gpose[6])
 {
@@ -711,6 +712,13 @@ int or_render_grad(const float *vol, const or_grid *g, const double pose[6], con
         double *pos = malloc(sizeof(double) * 3 * (size_t)(S + 1));
         double *Z = malloc(sizeof(double) * (size_t)(S + 1));
         double *gZ = gZall + (long)j * (S + 1);
+        int any = 0;
+        for (int k = 0; k < S && !any; k++) any = gy[(long)j * S + k] != 0.0;
+        if (!any) {
+            memset(gZ, 0, sizeof(double) * (size_t)(S + 1));
+            free(pos); free(Z);
+            continue;
+        }
         double *m = malloc(sizeof(double) * (size_t)S);
         double *gd0 = calloc((size_t)S + 1, sizeof(double));
         or_ray_positions(pose, fan, j, pos);

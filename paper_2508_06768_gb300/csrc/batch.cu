@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kBlurWarps * 32) k_batch_blur(const float *__r
     for (int64_t t = (int64_t)blockIdx.x * kBlurWarps + (threadIdx.x >> 5); t < n_tiles; t += nw) {
         const BlurTile tl = tiles[t];
         const PlanPose pp = poses[tl.pose];
-        blur_strip<TRANSPOSE, WT>(in + pp.img_off, out + pp.img_off, pp.n_rays, pp.S, b, tl.k0);
+        blur_strip<TRANSPOSE, WT>(in + pp.img_off, out + pp.img_off, pp.n_rays, pp.S, b, tl.k0, 0, pp.n_rays);
     }
 }
 

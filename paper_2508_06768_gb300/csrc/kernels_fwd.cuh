@@ -130,19 +130,21 @@ __device__ __forceinline__ float blur_w(const BlurArgs &b, int m, int k, float i
 }
 
 // Lateral blur of one pose image (Section 2.4), or its transpose, on one
-// strip of 32 echo rows [k0, k0 + 32) (one row per lane) across all n rays.
+// strip of 32 echo rows [k0, k0 + 32) (one row per lane), output rays
+// [j0, j1) of the n rays.
 // in/out: [n][S].
 // Forward:   out[j] = sum_m w_m in[j+m] / N_j        (valid j+m)
 // Transpose: out[j] = sum_m w_m in[j+m] / N_{j+m}    (valid j+m)
 // with N_j = sum of w_m over the valid j+m.  The warp sweeps the rays once:
 // every input element is read once, kBlurStep rows at a time into a
 // register window of kBlurStep + 2W rows, and every output is written once,
-// each access a coalesced 128-byte row segment.  WT >= 0 is the half-width
+// each access a coalesced 128-byte row segment (a ray range other than the
+// whole fan also reads its 2W halo rays).  WT >= 0 is the half-width
 // known at compile time; WT < 0 is the general path for wide kernels, which
 // reads the window through the cache instead.
 template <bool TRANSPOSE, int WT>
 __device__ void blur_strip(const float *__restrict__ in, float *__restrict__ out, int n, int S,
-                           const BlurArgs &b, int k0)
+                           const BlurArgs &b, int k0, int j0, int j1)
 {
     const int lane = threadIdx.x & 31;
     const int k = k0 + lane;
@@ -176,8 +178,8 @@ __device__ void blur_strip(const float *__restrict__ in, float *__restrict__ out
         };
         float win[B + 2 * WW];
 #pragma unroll
-        for (int t = 0; t < 2 * WW; t++) win[t] = ld(t - WW);
-        for (int jb = 0; jb < n; jb += B) {
+        for (int t = 0; t < 2 * WW; t++) win[t] = ld(j0 + t - WW);
+        for (int jb = j0; jb < j1; jb += B) {
             float nx[B];
 #pragma unroll
             for (int t = 0; t < B; t++) nx[t] = (kin && jb + WW + t < n) ? __ldg(src + (size_t)(jb + WW + t) * S) : 0.0f;
@@ -190,7 +192,7 @@ __device__ void blur_strip(const float *__restrict__ in, float *__restrict__ out
                 float acc = w[0] * win[i + WW];
 #pragma unroll
                 for (int m = 1; m <= WW; m++) acc = fmaf(w[m], win[i + WW - m] + win[i + WW + m], acc);
-                if (kin && j < n) {
+                if (kin && j < j1) {
                     if (!TRANSPOSE) acc *= rnorm(j);
                     dst[(size_t)j * S] = acc;
                 }
@@ -215,7 +217,7 @@ __device__ void blur_strip(const float *__restrict__ in, float *__restrict__ out
         if (TRANSPOSE) x *= 1.0f / N_of(j);
         return x;
     };
-    for (int j = 0; j < n; j++) {
+    for (int j = j0; j < j1; j++) {
         float acc = wt(0) * ld(j);
         for (int m = 1; m <= W; m++) acc = fmaf(wt(m), ld(j - m) + ld(j + m), acc);
         if (!TRANSPOSE) acc *= 1.0f / N_of(j);
@@ -223,14 +225,18 @@ __device__ void blur_strip(const float *__restrict__ in, float *__restrict__ out
     }
 }
 
-// Single-pose blur: one warp per strip.
+// Single-pose blur: one warp per strip and range of kBlurSegRays rays (one
+// pose alone is too small a grid for whole-fan strips).
+constexpr int kBlurSegRays = 64;
+
 template <bool TRANSPOSE, int WT>
 __global__ void __launch_bounds__(kBlurWarps * 32) k_blur(const float *__restrict__ in, float *__restrict__ out,
                                                           int n, int S, BlurArgs b)
 {
     const int strip = blockIdx.x * kBlurWarps + (threadIdx.x >> 5);
     if (strip * kBlurRows >= S) return;
-    blur_strip<TRANSPOSE, WT>(in, out, n, S, b, strip * kBlurRows);
+    const int j0 = blockIdx.y * kBlurSegRays;
+    blur_strip<TRANSPOSE, WT>(in, out, n, S, b, strip * kBlurRows, j0, min(n, j0 + kBlurSegRays));
 }
 
 }  // namespace dfs

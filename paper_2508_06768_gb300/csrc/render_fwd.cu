@@ -81,7 +81,7 @@ int launch_blur(const float *in, float *out, int n, int S, const diffus_params *
 {
     BlurArgs b{(float)prm->sigma0, (float)prm->sigma1, blur_halfwidth(prm)};
     const int strips = (S + kBlurRows - 1) / kBlurRows;
-    const int grid = (strips + kBlurWarps - 1) / kBlurWarps;
+    const dim3 grid((strips + kBlurWarps - 1) / kBlurWarps, (n + kBlurSegRays - 1) / kBlurSegRays);
 #define DFS_BLUR(WT)                                                        \
     if (transpose)                                                          \
         k_blur<true, WT><<<grid, kBlurWarps * 32, 0, s>>>(in, out, n, S, b); \

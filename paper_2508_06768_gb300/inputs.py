@@ -245,6 +245,11 @@ def fine_brain_phantom(n=512, spacing=0.5, seed=5, texture_sigma=0.02):
     """n^3 volume at `spacing` mm: the brain recipe built at twice the spacing,
     upsampled 2x by linear interpolation, plus a fine iid texture of
     `texture_sigma` MRayl (its 0.3 mm correlation length is below one voxel)."""
+    key = "fine_brain_%d_%g_%d_%g" % (n, spacing, seed, texture_sigma)
+    return _cached(key, lambda: _fine_brain_phantom(n, spacing, seed, texture_sigma))
+
+
+def _fine_brain_phantom(n, spacing, seed, texture_sigma):
     coarse = brain_phantom((n // 2, n // 2, n // 2), spacing * 2, seed=seed)
     c = coarse.data.astype(np.float32)
     # 2x linear upsampling along each axis (voxel centres of the fine grid
