@@ -155,7 +155,7 @@ __global__ void k_batch_setup(const float *__restrict__ poses, BatchDev B, VolPl
 
 // Persistent forward: each warp takes rays from the queue (longest first).
 template <typename T, int WARPS, bool REFINE>
-__global__ void __launch_bounds__(WARPS * 32) k_batch_fwd(const T *__restrict__ vol, MarchArgs A, BatchDev B,
+__global__ void __launch_bounds__(WARPS * 32, REFINE ? 1 : kFwdThreadsPerSM / (WARPS * 32)) k_batch_fwd(const T *__restrict__ vol, MarchArgs A, BatchDev B,
                                                           const RayGeo *__restrict__ geo, float *__restrict__ out,
                                                           int *__restrict__ valid, uint32_t *__restrict__ status,
                                                           unsigned *__restrict__ counter, float4 *__restrict__ ckpt,
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_batch_fwd(const T *__restrict__ 
 }
 
 template <typename T, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_batch_bwd(const T *__restrict__ vol, MarchArgs A, BatchDev B,
+__global__ void __launch_bounds__(WARPS * 32, kBwdThreadsPerSM / (WARPS * 32)) k_batch_bwd(const T *__restrict__ vol, MarchArgs A, BatchDev B,
                                                           const RayGeo *__restrict__ geo,
                                                           const float *__restrict__ gy, float *__restrict__ gz,
                                                           double *__restrict__ part, float4 *__restrict__ ckpt,

@@ -241,45 +241,44 @@ __global__ void k_unit_counts(const uint32_t *__restrict__ bstart, const uint32_
     ucount[b] = (c + kUnitRuns - 1) / kUnitRuns;
 }
 
-// One CTA per unit (grid-stride): gather the unit's runs into its 9^3 partial.
+// Unit -> brick table: brick b owns units ustart[b] .. ustart[b] + ucount[b] - 1.
+__global__ void k_unit_bricks(const uint32_t *__restrict__ ustart, const uint32_t *__restrict__ ucount, int nb,
+                              uint32_t *__restrict__ unit_brick)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const uint32_t u0 = ustart[b], c = ucount[b];
+    for (uint32_t i = 0; i < c; i++) unit_brick[u0 + i] = (uint32_t)b;
+}
+
+// One warp per unit (grid-stride over all warps): the warp gathers the
+// unit's runs into its own 9^3 accumulator and writes the unit's partial.
+// Warps are independent, so a CTA has no block barriers.
 __global__ void __launch_bounds__(kGatherWarps * 32)
     k_gather_units(const RayGeo *__restrict__ geo, const float *__restrict__ gz, const long long *__restrict__ gz_off,
                    const Run *__restrict__ runs, const uint32_t *__restrict__ sorted_vals,
                    const uint32_t *__restrict__ bstart, const uint32_t *__restrict__ bend,
-                   const uint32_t *__restrict__ ustart, const uint32_t *__restrict__ n_units, int nb, GatherArgs G,
-                   float *__restrict__ upart)
+                   const uint32_t *__restrict__ ustart, const uint32_t *__restrict__ unit_brick,
+                   const uint32_t *__restrict__ n_units, GatherArgs G, float *__restrict__ upart)
 {
     __shared__ GatherSmem sm;
-    const int w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t total = *n_units;
-    for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
-        // brick of unit u: last b with ustart[b] <= u
-        int lo = 0, hi = nb - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (ustart[mid] <= u) lo = mid; else hi = mid - 1;
-        }
-        const int b = lo;
+    float *acc = sm.acc[w];
+    for (uint32_t u = blockIdx.x * kGatherWarps + w; u < total; u += gridDim.x * kGatherWarps) {
+        const int b = (int)unit_brick[u];
         const uint32_t part = u - ustart[b];
         const uint32_t r0 = bstart[b] + part * kUnitRuns;
         uint32_t r1 = r0 + kUnitRuns;
         r1 = r1 < bend[b] ? r1 : bend[b];
         const int bx0 = (b % G.nbx) * kBrick, by0 = ((b / G.nbx) % G.nby) * kBrick, bz0 = (b / (G.nbx * G.nby)) * kBrick;
-        for (int i = threadIdx.x; i < kGatherWarps * kBrickVox; i += blockDim.x) (&sm.acc[0][0])[i] = 0.0f;
-        __syncthreads();
-        // warp w takes the w-th quarter of the unit's runs (in ray order)
-        const uint32_t n = r1 - r0, per = (n + kGatherWarps - 1) / kGatherWarps;
-        const uint32_t qa = r0 + min(n, per * w), qb = r0 + min(n, per * (w + 1));
-        if (qa < qb) gather_runs(runs, sorted_vals, qa, qb, geo, gz, gz_off, G, bx0, by0, bz0, sm, w);
-        __syncthreads();
+        for (int i = lane; i < kBrickVox; i += 32) acc[i] = 0.0f;
+        __syncwarp();
+        gather_runs(runs, sorted_vals, r0, r1, geo, gz, gz_off, G, bx0, by0, bz0, sm, w);
+        __syncwarp();
         float *out = upart + (size_t)u * kBrickVox;
-        for (int v = threadIdx.x; v < kBrickVox; v += blockDim.x) {
-            float s = sm.acc[0][v];
-#pragma unroll
-            for (int q = 1; q < kGatherWarps; q++) s += sm.acc[q][v];
-            out[v] = s;
-        }
-        __syncthreads();
+        for (int i = lane; i < kBrickVox; i += 32) out[i] = acc[i];
+        __syncwarp();
     }
 }
 
@@ -356,7 +355,7 @@ struct GatherLayout {
     Run *runs;
     uint32_t *keys[2], *vals[2];
     uint32_t *hist, *sums, *misc;   // misc: [0] units total, [1] scan total
-    uint32_t *bstart, *bend, *ucount, *ustart;
+    uint32_t *bstart, *bend, *ucount, *ustart, *unit_brick;
     float *upart;
     size_t bytes;
 };
@@ -384,6 +383,7 @@ static GatherLayout gather_layout(void *ws, const diffus_volume_desc *vd, long l
     L.bend = c.take<uint32_t>(nb);
     L.ucount = c.take<uint32_t>(nb);
     L.ustart = c.take<uint32_t>(nb);
+    L.unit_brick = c.take<uint32_t>(max_units);
     L.upart = c.take<float>(max_units * kBrickVox);
     L.bytes = c.used;
     return L;
@@ -434,9 +434,10 @@ int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_r
     k_brick_bounds<<<(unsigned)((slots + 255) / 256), 256, 0, s>>>(L.keys[cur], slots, sentinel, L.bstart, L.bend);
     k_unit_counts<<<(nb + 255) / 256, 256, 0, s>>>(L.bstart, L.bend, nb, L.ucount);
     launch_scan(L.ucount, L.ustart, (size_t)nb, L.sums, L.misc + 0, s);
+    k_unit_bricks<<<(nb + 255) / 256, 256, 0, s>>>(L.ustart, L.ucount, nb, L.unit_brick);
     record_mark(marks.units, marks.external, s);
     k_gather_units<<<sms * ctas_per_sm, kGatherWarps * 32, 0, s>>>(geo, gz, gz_off, L.runs, L.vals[cur], L.bstart, L.bend,
-                                                         L.ustart, L.misc + 0, nb, G, L.upart);
+                                                                  L.ustart, L.unit_brick, L.misc + 0, G, L.upart);
     record_mark(marks.reduce, marks.external, s);
     const size_t nv = (size_t)vd->nx * vd->ny * vd->nz;
     k_voxel_reduce<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(L.upart, L.ustart, L.ucount, G, grad_vol);

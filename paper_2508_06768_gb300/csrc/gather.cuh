@@ -11,13 +11,12 @@
 //             order whatever the launch schedule.
 //  3. units:  each brick's runs are cut into units of at most kUnitRuns runs
 //             (hot bricks crossed by many poses spread over many CTAs).
-//  4. gather: one CTA per unit accumulates its samples into the 9^3 voxels
-//             the brick's cells touch, in per-warp shared-memory copies.
-//             Each lane walks one run and sums its samples per cell in
-//             registers; closed cell records on equal cells are combined
-//             in lane order and written one corner at a time, so no two
-//             lanes update a voxel at once.  Copies are combined in a fixed
-//             order into the unit's partial.
+//  4. gather: one warp per unit accumulates its samples into the 9^3 voxels
+//             the brick's cells touch, in a shared-memory copy of its own.
+//             Each lane walks one run, one cell at a time, summing moments
+//             of dL/dZ; cell records on equal cells are combined in lane
+//             order and written one corner at a time, so no two lanes
+//             update a voxel at once.  The copy is the unit's partial.
 //  5. reduce: each voxel sums the partials of the units of the (up to 8)
 //             bricks whose cells touch it, in a fixed order.
 //
@@ -94,20 +93,6 @@ struct GatherSmem {
     float acc[kGatherWarps][kBrickVox];
 };
 
-// Cell index and weight of one axis.  CLAMP = false is the fast path for a
-// run that never leaves the volume: identical results to axis_split there.
-template <bool CLAMP>
-__device__ __forceinline__ void gather_axis(long long X, int n, int &i0, float &f)
-{
-    if (CLAMP) {
-        bool in;
-        axis_split(X, n, i0, f, in);
-    } else {
-        i0 = (int)(X >> 32);
-        f = __uint_as_float(0x3F800000u | ((unsigned)X >> 9)) - 1.0f;
-    }
-}
-
 // Adds one closed cell record per flagged lane into the warp's accumulator.
 // Records on the same cell are grouped with a warp match and added into the
 // group's lowest lane in lane order; the group leaders, all on distinct
@@ -145,15 +130,62 @@ __device__ __forceinline__ void flush_records(bool fl, int fcell, float (&fv)[8]
     }
 }
 
-constexpr int kGSteps = 16;    // samples a lane may merge into one cell record per step
+constexpr int kGCellCap = 32;  // samples of one cell record at most (bounds the moment orders)
+
+// One axis of a run position inside its current cell: the cell index i, and
+// the trilinear weight of the upper corner as u + v k for the next samples
+// k = 0, 1, ... (exact in the clamped regions, where v = 0), plus the number
+// of samples before the cell or the clamping changes (at most cap).
+// Boundaries are found exactly on the fixed-point line: the float estimate
+// of ceil(num / den) is corrected with integer tests.
+__device__ __forceinline__ int ceil_div_fixed(long long num, long long den, int cap)
+{
+    // smallest k >= 1 with k den >= num (num >= 1, den >= 1), at most cap
+    float est = ceilf((float)num / (float)den);
+    long long k = est < 1.0f ? 1 : (est > (float)cap ? cap : (long long)est);
+    while (k > 1 && (k - 1) * den >= num) k--;
+    while (k < cap && k * den < num) k++;
+    return (int)k;
+}
+
+__device__ __forceinline__ void axis_run(long long X, long long dX, int n, int cap, int &i, float &u, float &v,
+                                         int &steps)
+{
+    const long long top = (long long)(n - 1) << 32;
+    if (X < 0) {                                  // clamped below: weight 0 until X reaches 0
+        i = 0;
+        u = 0.0f;
+        v = 0.0f;
+        steps = dX > 0 ? ceil_div_fixed(-X, dX, cap) : cap;
+    } else if (X >= top) {                        // clamped above: weight 1 until X drops below the top
+        i = n - 2;
+        u = 1.0f;
+        v = 0.0f;
+        steps = dX < 0 ? ceil_div_fixed(X - top + 1, -dX, cap) : cap;
+    } else {
+        const long long c = X >> 32;
+        i = (int)c;
+        u = __uint_as_float(0x3F800000u | ((unsigned)X >> 9)) - 1.0f;   // 23-bit fraction
+        v = (float)dX * 2.3283064365386963e-10f;                        // dX / 2^32
+        if (dX > 0)
+            steps = ceil_div_fixed(((c + 1) << 32) - X, dX, cap);
+        else if (dX < 0)
+            steps = ceil_div_fixed(X - (c << 32) + 1, -dX, cap);
+        else
+            steps = cap;
+    }
+}
 
 // Gather the runs [q0, q1) of one brick (first cell (bx0, by0, bz0)) into
-// this warp's 9^3 accumulator.  Each lane walks one run; per warp step it
-// advances up to kGSteps samples while they stay in one cell, summing the
-// samples' 8 trilinear weights into that cell's record, and the warp then
-// flushes the step's records together.  A lane whose run ends takes the next
-// run in order, so every decision depends only on the data and the sums
-// have a fixed order.
+// this warp's 9^3 accumulator.  Each lane walks one run, one cell at a
+// time.  Inside a cell the upper-corner weights along each axis are linear
+// in the sample index k (u + v k), so each of the cell's 8 trilinear corner
+// sums sum_k g_k w_x(k) w_y(k) w_z(k) is a fixed combination of the four
+// moments sum_k g_k k^j (j = 0..3): the sample loop only accumulates the
+// moments, and the corner sums are formed once per cell.  The warp then
+// flushes the step's cell records together.  A lane whose run ends takes
+// the next run in order, so every decision depends only on the data and
+// the sums have a fixed order.
 __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const uint32_t *__restrict__ order,
                                             uint32_t q0, uint32_t q1, const RayGeo *__restrict__ geo,
                                             const float *__restrict__ gzbuf, const long long *__restrict__ gz_off,
@@ -165,7 +197,6 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
     long long X = 0, Y = 0, Z = 0, dX = 0, dY = 0, dZ = 0;
     const float *g = gzbuf;
     int left = 0;                 // samples left in the lane's run
-    bool clamp = false;
     uint32_t next = q0;           // next unassigned run (warp-uniform)
     for (;;) {
         // refill idle lanes in lane order
@@ -183,52 +214,66 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
                 dZ = geo[run.ray].DX[2];
                 g = gzbuf + gz_off[run.ray] + run.k0;
                 left = run.k1 - run.k0 + 1;
-                clamp = run.clamp != 0;
             }
             next += __popc(idles);
         }
         if (!__any_sync(0xffffffffu, left > 0)) break;
-        // advance up to kGSteps samples within one cell
-        int cell = -1;
-        float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        bool more = left > 0;
-#pragma unroll 2
-        for (int t = 0; t < kGSteps; t++) {
-            if (more) {
-                int ix, iy, iz;
-                float fx, fy, fz;
-                if (clamp) {
-                    gather_axis<true>(X, G.nx, ix, fx);
-                    gather_axis<true>(Y, G.ny, iy, fy);
-                    gather_axis<true>(Z, G.nz, iz, fz);
-                } else {
-                    gather_axis<false>(X, G.nx, ix, fx);
-                    gather_axis<false>(Y, G.ny, iy, fy);
-                    gather_axis<false>(Z, G.nz, iz, fz);
-                }
-                const int c = (ix - bx0) | ((iy - by0) << 3) | ((iz - bz0) << 6);
-                if (cell >= 0 && c != cell) {
-                    more = false;            // the next record starts here
-                } else {
-                    cell = c;
-                    const float gs = __ldg(g);
-                    const float wx1 = fx, wx0 = 1.0f - fx, wy1 = fy, wy0 = 1.0f - fy;
-                    const float gz0 = gs * (1.0f - fz), gz1 = gs * fz;
-                    const float a00 = gz0 * wy0, a10 = gz0 * wy1, a01 = gz1 * wy0, a11 = gz1 * wy1;
-                    v[0] = fmaf(a00, wx0, v[0]); v[1] = fmaf(a00, wx1, v[1]);
-                    v[2] = fmaf(a10, wx0, v[2]); v[3] = fmaf(a10, wx1, v[3]);
-                    v[4] = fmaf(a01, wx0, v[4]); v[5] = fmaf(a01, wx1, v[5]);
-                    v[6] = fmaf(a11, wx0, v[6]); v[7] = fmaf(a11, wx1, v[7]);
-                    X += dX;
-                    Y += dY;
-                    Z += dZ;
-                    g++;
-                    if (--left == 0) more = false;
-                }
-            }
-            if (!__any_sync(0xffffffffu, more)) break;
+        // the lane's current cell and its sample count
+        int ix = 0, iy = 0, iz = 0, len = 0;
+        float ux = 0.0f, vx = 0.0f, uy = 0.0f, vy = 0.0f, uz = 0.0f, vz = 0.0f;
+        if (left > 0) {
+            int sx, sy, sz;
+            const int cap = min(left, kGCellCap);
+            axis_run(X, dX, G.nx, cap, ix, ux, vx, sx);
+            axis_run(Y, dY, G.ny, cap, iy, uy, vy, sy);
+            axis_run(Z, dZ, G.nz, cap, iz, uz, vz, sz);
+            len = min(min(sx, sy), min(sz, cap));
         }
-        flush_records(cell >= 0, cell, v, acc, lane, lt);
+        // moments of dL/dZ over the cell's samples
+        float M0 = 0.0f, M1 = 0.0f, M2 = 0.0f, M3 = 0.0f;
+        const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+#pragma unroll 4
+        for (int k = 0; k < kmax; k++) {
+            if (k < len) {
+                const float gk = __ldg(g + k);
+                const float kf = (float)k;
+                M0 += gk;
+                float t = gk * kf;
+                M1 += t;
+                t *= kf;
+                M2 += t;
+                M3 = fmaf(t, kf, M3);
+            }
+        }
+        // corner sums: yz products as quadratics in k, then the x factors
+        float v[8];
+        {
+            const float ay[2] = {1.0f - uy, uy}, by[2] = {-vy, vy};
+            const float az[2] = {1.0f - uz, uz}, bz[2] = {-vz, vz};
+            const float ax0 = 1.0f - ux, bx0 = -vx;
+#pragma unroll
+            for (int zz = 0; zz < 2; zz++)
+#pragma unroll
+                for (int yy = 0; yy < 2; yy++) {
+                    const float q0c = ay[yy] * az[zz];
+                    const float q1c = fmaf(ay[yy], bz[zz], by[yy] * az[zz]);
+                    const float q2c = by[yy] * bz[zz];
+                    const float A = fmaf(q2c, M2, fmaf(q1c, M1, q0c * M0));
+                    const float B = fmaf(q2c, M3, fmaf(q1c, M2, q0c * M1));
+                    v[(zz << 2) | (yy << 1)] = fmaf(bx0, B, ax0 * A);
+                    v[(zz << 2) | (yy << 1) | 1] = fmaf(vx, B, ux * A);
+                }
+        }
+        const bool has = len > 0;
+        const int cell = (ix - bx0) | ((iy - by0) << 3) | ((iz - bz0) << 6);
+        if (has) {
+            X += (long long)len * dX;
+            Y += (long long)len * dY;
+            Z += (long long)len * dZ;
+            g += len;
+            left -= len;
+        }
+        flush_records(has, cell, v, acc, lane, lt);
     }
 }
 

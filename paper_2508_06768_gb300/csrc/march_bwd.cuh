@@ -23,6 +23,7 @@ constexpr int kBwdPad = 289;   // smem_idx(256) + 1
 struct BwdSmem {
     float zr[kBwdPad], dz[kBwdPad];   // samples base .. base+256 (zref + dz form)
     float gx[kBwdPad], gy[kBwdPad], gz[kBwdPad];
+    double acc[6];                    // the ray's pose-gradient sums (lane 0)
 };
 
 // Echo of one interface and its partial derivatives with respect to the
@@ -92,7 +93,9 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
     float lam0 = 0.0f, lam1 = 0.0f, mus = 0.0f;   // adjoint at the end of the current segment
     float carry_gz1 = 0.0f;                       // dL/dZ of sample base+256 from interface base+256
     float czr = 0.0f, cdz = 0.0f, cg0 = 0.0f, cg1 = 0.0f, cg2 = 0.0f;   // sample base+256
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double *acc = sm.acc;
+    if (lane == 0)
+        for (int q = 0; q < 6; q++) acc[q] = 0.0;
     const float ds = rg.ds;
 
     for (int s = nseg - 1; s >= 0; s--) {
