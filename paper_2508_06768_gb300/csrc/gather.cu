@@ -14,13 +14,8 @@ constexpr int kScanChunk = 4096;
 
 // ------------------------------------------------------------------ runs
 
-// Position inside the box where trilinear sampling needs no clamping.
-__device__ __forceinline__ bool inside(long long X, long long Y, long long Z, const GatherArgs &G)
-{
-    return X >= 0 && (X >> 32) < G.nx - 1 && Y >= 0 && (Y >> 32) < G.ny - 1 && Z >= 0 && (Z >> 32) < G.nz - 1;
-}
-
-__global__ void k_ray_runs(const RayGeo *__restrict__ geo, int n_rays, GatherArgs G, int cap, uint32_t sentinel,
+__global__ void k_ray_runs(const RayGeo *__restrict__ geo, const long long *__restrict__ gz_off, int n_rays,
+                           GatherArgs G, int cap, uint32_t sentinel,
                            Run *__restrict__ runs, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
                            uint32_t *__restrict__ status)
 {
@@ -37,7 +32,7 @@ __global__ void k_ray_runs(const RayGeo *__restrict__ geo, int n_rays, GatherArg
     }
     long long k = 0;
     int cnt = 0;
-    const size_t base = (size_t)r * cap;
+    // slot of run i of ray r: i * n_rays + r (consecutive rays write consecutive slots)
     while (k <= S) {
         long long kn = nxt[0];
         kn = nxt[1] < kn ? nxt[1] : kn;
@@ -49,16 +44,16 @@ __global__ void k_ray_runs(const RayGeo *__restrict__ geo, int n_rays, GatherArg
             run.X = rg.X0[0] + k * rg.DX[0];
             run.Y = rg.X0[1] + k * rg.DX[1];
             run.Z = rg.X0[2] + k * rg.DX[2];
-            run.ray = r;
-            run.k0 = (int)k;
-            run.k1 = (int)k1;
-            // the inner box is convex: the run is clamp-free iff both ends are inside
-            run.clamp = !(inside(run.X, run.Y, run.Z, G) &&
-                          inside(rg.X0[0] + k1 * rg.DX[0], rg.X0[1] + k1 * rg.DX[1], rg.X0[2] + k1 * rg.DX[2], G));
-            run.pad[0] = run.pad[1] = 0;
-            runs[base + cnt] = run;
-            keys[base + cnt] = brick;
-            vals[base + cnt] = (uint32_t)(base + cnt);
+            run.dX = rg.DX[0];
+            run.dY = rg.DX[1];
+            run.dZ = rg.DX[2];
+            run.g_off = gz_off[r] + k;
+            run.len = (int)(k1 - k + 1);
+            run.pad = 0;
+            const size_t slot = (size_t)cnt * n_rays + r;
+            runs[slot] = run;
+            keys[slot] = brick;
+            vals[slot] = (uint32_t)slot;
             cnt++;
         } else if (status) {
             atomicOr(status + 2, (uint32_t)DIFFUS_STATUS_QUEUE);
@@ -75,8 +70,9 @@ __global__ void k_ray_runs(const RayGeo *__restrict__ geo, int n_rays, GatherArg
         }
     }
     for (int i = cnt; i < cap; i++) {
-        keys[base + i] = sentinel;
-        vals[base + i] = (uint32_t)(base + i);
+        const size_t slot = (size_t)i * n_rays + r;
+        keys[slot] = sentinel;
+        vals[slot] = (uint32_t)slot;
     }
 }
 
@@ -255,8 +251,7 @@ __global__ void k_unit_bricks(const uint32_t *__restrict__ ustart, const uint32_
 // unit's runs into its own 9^3 accumulator and writes the unit's partial.
 // Warps are independent, so a CTA has no block barriers.
 __global__ void __launch_bounds__(kGatherWarps * 32)
-    k_gather_units(const RayGeo *__restrict__ geo, const float *__restrict__ gz, const long long *__restrict__ gz_off,
-                   const Run *__restrict__ runs, const uint32_t *__restrict__ sorted_vals,
+    k_gather_units(const float *__restrict__ gz, const Run *__restrict__ runs, const uint32_t *__restrict__ sorted_vals,
                    const uint32_t *__restrict__ bstart, const uint32_t *__restrict__ bend,
                    const uint32_t *__restrict__ ustart, const uint32_t *__restrict__ unit_brick,
                    const uint32_t *__restrict__ n_units, GatherArgs G, float *__restrict__ upart)
@@ -274,7 +269,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
         const int bx0 = (b % G.nbx) * kBrick, by0 = ((b / G.nbx) % G.nby) * kBrick, bz0 = (b / (G.nbx * G.nby)) * kBrick;
         for (int i = lane; i < kBrickVox; i += 32) acc[i] = 0.0f;
         __syncwarp();
-        gather_runs(runs, sorted_vals, r0, r1, geo, gz, gz_off, G, bx0, by0, bz0, sm, w);
+        gather_runs(runs, sorted_vals, r0, r1, gz, G, bx0, by0, bz0, sm, w);
         __syncwarp();
         float *out = upart + (size_t)u * kBrickVox;
         for (int i = lane; i < kBrickVox; i += 32) out[i] = acc[i];
@@ -417,7 +412,7 @@ int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_r
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 
-    k_ray_runs<<<(unsigned)((n_rays + 127) / 128), 128, 0, s>>>(geo, (int)n_rays, G, cap, sentinel, L.runs, L.keys[0],
+    k_ray_runs<<<(unsigned)((n_rays + 127) / 128), 128, 0, s>>>(geo, gz_off, (int)n_rays, G, cap, sentinel, L.runs, L.keys[0],
                                                                L.vals[0], status);
     // stable LSD radix sort by brick
     const int nblk = (int)((slots + kSortTile - 1) / kSortTile);
@@ -436,7 +431,7 @@ int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_r
     launch_scan(L.ucount, L.ustart, (size_t)nb, L.sums, L.misc + 0, s);
     k_unit_bricks<<<(nb + 255) / 256, 256, 0, s>>>(L.ustart, L.ucount, nb, L.unit_brick);
     record_mark(marks.units, marks.external, s);
-    k_gather_units<<<sms * ctas_per_sm, kGatherWarps * 32, 0, s>>>(geo, gz, gz_off, L.runs, L.vals[cur], L.bstart, L.bend,
+    k_gather_units<<<sms * ctas_per_sm, kGatherWarps * 32, 0, s>>>(gz, L.runs, L.vals[cur], L.bstart, L.bend,
                                                                   L.ustart, L.unit_brick, L.misc + 0, G, L.upart);
     record_mark(marks.reduce, marks.external, s);
     const size_t nv = (size_t)vd->nx * vd->ny * vd->nz;

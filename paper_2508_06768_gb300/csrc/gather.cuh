@@ -6,9 +6,10 @@
 //  1. runs:   every ray walks the bricks its (clamped) cells pass through, a
 //             3D DDA on the exact fixed-point line; clamping is monotone
 //             along a ray, so each brick is one run [k0, k1] of samples.
-//  2. sort:   the runs, written at fixed per-ray slots, are sorted by brick
-//             with a stable radix sort, so every brick's runs appear in ray
-//             order whatever the launch schedule.
+//  2. sort:   the runs, written at fixed slots (run i of ray r at slot
+//             i * n_rays + r), are sorted by brick with a stable radix sort,
+//             so every brick's runs appear in slot order whatever the launch
+//             schedule.
 //  3. units:  each brick's runs are cut into units of at most kUnitRuns runs
 //             (hot bricks crossed by many poses spread over many CTAs).
 //  4. gather: one warp per unit accumulates its samples into the 9^3 voxels
@@ -39,16 +40,18 @@ struct GatherArgs {
     int nbx, nby, nbz;                // bricks of cells per axis (cells 0..n-2)
 };
 
-// Samples k0..k1 of ray `ray` lie in cells of one brick.  The run also
-// carries the fixed-point position of sample k0 and whether any of its
-// samples is clamped to the border, so a gather lane starts it from one
-// record.
+// Samples k0 .. k0+len-1 of one ray lie in cells of one brick.  The run
+// carries all a gather lane needs to walk it: the fixed-point position of
+// its first sample, the ray's step, and the offset of its first dL/dZ
+// value.
 struct alignas(16) Run {
     long long X, Y, Z;
-    int ray, k0, k1, clamp;
-    int pad[2];
+    long long dX, dY, dZ;
+    long long g_off;
+    int len;
+    int pad;
 };
-static_assert(sizeof(Run) == 48, "Run layout");
+static_assert(sizeof(Run) == 64, "Run layout");
 
 // First k in [0, kmax+1] with X0 + k DX >= L for DX > 0, or kmax+1 if no
 // k <= kmax qualifies.  Exact in fixed point: the float estimate is off by
@@ -187,8 +190,7 @@ __device__ __forceinline__ void axis_run(long long X, long long dX, int n, int c
 // the next run in order, so every decision depends only on the data and
 // the sums have a fixed order.
 __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const uint32_t *__restrict__ order,
-                                            uint32_t q0, uint32_t q1, const RayGeo *__restrict__ geo,
-                                            const float *__restrict__ gzbuf, const long long *__restrict__ gz_off,
+                                            uint32_t q0, uint32_t q1, const float *__restrict__ gzbuf,
                                             const GatherArgs &G, int bx0, int by0, int bz0, GatherSmem &sm, int w)
 {
     const int lane = threadIdx.x & 31;
@@ -198,24 +200,28 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
     const float *g = gzbuf;
     int left = 0;                 // samples left in the lane's run
     uint32_t next = q0;           // next unassigned run (warp-uniform)
+    // lane i holds the index of run next + i, loaded one refill ahead
+    uint32_t pre = next + lane < q1 ? order[next + lane] : 0u;
     for (;;) {
         // refill idle lanes in lane order
         const bool idle = left == 0;
         const unsigned idles = __ballot_sync(0xffffffffu, idle);
         if (idles && next < q1) {
-            const uint32_t mine = next + __popc(idles & lt);
-            if (idle && mine < q1) {
-                const Run run = runs[order[mine]];
+            const int src = __popc(idles & lt);
+            const uint32_t idx = __shfl_sync(0xffffffffu, pre, src);
+            if (idle && next + src < q1) {
+                const Run run = runs[idx];
                 X = run.X;
                 Y = run.Y;
                 Z = run.Z;
-                dX = geo[run.ray].DX[0];
-                dY = geo[run.ray].DX[1];
-                dZ = geo[run.ray].DX[2];
-                g = gzbuf + gz_off[run.ray] + run.k0;
-                left = run.k1 - run.k0 + 1;
+                dX = run.dX;
+                dY = run.dY;
+                dZ = run.dZ;
+                g = gzbuf + run.g_off;
+                left = run.len;
             }
             next += __popc(idles);
+            pre = next + lane < q1 ? order[next + lane] : 0u;
         }
         if (!__any_sync(0xffffffffu, left > 0)) break;
         // the lane's current cell and its sample count
