@@ -15,6 +15,7 @@ Section 2.4) in double precision.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -83,6 +84,10 @@ def _load():
                                            C.c_uint32, dp, dp, dp]
             lib.or_num_threads.restype = C.c_int
             lib.or_philox_many.argtypes = [C.POINTER(C.c_uint32), C.c_long, C.c_uint64, C.POINTER(C.c_uint32)]
+            sc = [dp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double,
+                  C.c_double, C.c_double, dp]
+            lib.or_scan_convert.argtypes = sc
+            lib.or_scan_convert_T.argtypes = sc
             _lib = lib
     return _lib
 
@@ -281,3 +286,35 @@ def render_grad(vol, pose, fan, params, gimg, pose_ctr: int = 0, want_vol: bool 
     if rc != 0:
         raise FloatingPointError("singular depth system in oracle gradient")
     return gvol, gpose
+
+
+def fan_grid(fan, W, H):
+    """The default display grid of a fan: x over the fan's lateral extent
+    [-depth sin(fov/2), depth sin(fov/2)] (the apex-centred box for fov <=
+    180 degrees), z over [0, depth]; returns (W, H, x0, x1, z0, z1)."""
+    half = float(fan.depth) * math.sin(min(0.5 * float(fan.fov), 0.5 * math.pi))
+    return (int(W), int(H), -half, half, 0.0, float(fan.depth))
+
+
+def scan_convert(img, fan, grid):
+    """Bilinear scan conversion of a polar image [n_rays][S] onto the
+    Cartesian grid (W, H, x0, x1, z0, z1); returns [H][W]."""
+    img = _f64(img)
+    n, S = img.shape
+    W, H, x0, x1, z0, z1 = grid
+    out = np.zeros((H, W))
+    rc = _load().or_scan_convert(_dp(img), n, S, float(fan.fov), float(fan.depth), W, H, x0, x1, z0, z1, _dp(out))
+    if rc:
+        raise ValueError("scan conversion needs n_rays >= 2, n_samples >= 2 and a positive field of view")
+    return out
+
+
+def scan_convert_T(gout, fan, n, S, grid):
+    """Adjoint of scan_convert: [H][W] -> [n][S]."""
+    gout = _f64(gout)
+    W, H, x0, x1, z0, z1 = grid
+    g = np.zeros((n, S))
+    rc = _load().or_scan_convert_T(_dp(gout), n, S, float(fan.fov), float(fan.depth), W, H, x0, x1, z0, z1, _dp(g))
+    if rc:
+        raise ValueError("scan conversion needs n_rays >= 2, n_samples >= 2 and a positive field of view")
+    return g

@@ -771,3 +771,73 @@ void or_philox_many(const uint32_t *ctr, long n, uint64_t key, uint32_t *out)
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < n; i++) or_philox4x32_10(ctr + 4 * i, k, out + 4 * i);
 }
+
+/* ------------------------------------------------------------------
+ * Scan conversion (the fan-shaped display image of Section 2.4 / Fig. 3).
+ * The polar image img[n][S] (row j = ray j at beam angle theta_j, column k =
+ * echo row k at depth (k+1) ds) is resampled onto a W x H Cartesian grid of
+ * the imaging plane (x lateral, z axial, apex at the origin).  Pixel (ix, iz)
+ * has centre x = x0 + (ix + 1/2)(x1 - x0)/W, z = z0 + (iz + 1/2)(z1 - z0)/H,
+ * polar coordinates rho = |(x, z)|, theta = atan2(x, z), fractional ray index
+ * v = (theta + fov/2)(n - 1)/fov and fractional row u = rho/ds - 1.  Its value
+ * is the bilinear interpolation of img at (v, u) when 0 <= v <= n-1 and
+ * 0 <= u <= S-1, else 0.  out is [H][W].  Requires n >= 2 and S >= 2. */
+static int scan_coords(int n, int S, double fov, double depth, int W, int H, double x0, double x1, double z0,
+                       double z1, int ix, int iz, int *j0, int *k0, double *fv, double *fu)
+{
+    double ds = depth / (double)S;
+    double x = x0 + ((double)ix + 0.5) * (x1 - x0) / (double)W;
+    double z = z0 + ((double)iz + 0.5) * (z1 - z0) / (double)H;
+    double rho = sqrt(x * x + z * z), th = atan2(x, z);
+    double v = (th + 0.5 * fov) * (double)(n - 1) / fov;
+    double u = rho / ds - 1.0;
+    if (!(v >= 0.0 && v <= (double)(n - 1) && u >= 0.0 && u <= (double)(S - 1))) return 0;
+    int j = (int)floor(v), k = (int)floor(u);
+    if (j > n - 2) j = n - 2;
+    if (k > S - 2) k = S - 2;
+    *j0 = j;
+    *k0 = k;
+    *fv = v - (double)j;
+    *fu = u - (double)k;
+    return 1;
+}
+
+int or_scan_convert(const double *img, int n, int S, double fov, double depth, int W, int H, double x0, double x1,
+                    double z0, double z1, double *out)
+{
+    if (n < 2 || S < 2 || W < 1 || H < 1 || !(fov > 0.0)) return -1;
+    for (int iz = 0; iz < H; iz++)
+        for (int ix = 0; ix < W; ix++) {
+            int j, k;
+            double fv, fu;
+            double val = 0.0;
+            if (scan_coords(n, S, fov, depth, W, H, x0, x1, z0, z1, ix, iz, &j, &k, &fv, &fu)) {
+                const double *r0 = img + (long)j * S, *r1 = img + (long)(j + 1) * S;
+                val = (1.0 - fv) * (1.0 - fu) * r0[k] + fv * (1.0 - fu) * r1[k] + (1.0 - fv) * fu * r0[k + 1] +
+                      fv * fu * r1[k + 1];
+            }
+            out[(long)iz * W + ix] = val;
+        }
+    return 0;
+}
+
+/* Adjoint of or_scan_convert: gimg (overwritten) = transpose applied to gout. */
+int or_scan_convert_T(const double *gout, int n, int S, double fov, double depth, int W, int H, double x0,
+                      double x1, double z0, double z1, double *gimg)
+{
+    if (n < 2 || S < 2 || W < 1 || H < 1 || !(fov > 0.0)) return -1;
+    memset(gimg, 0, sizeof(double) * (size_t)n * S);
+    for (int iz = 0; iz < H; iz++)
+        for (int ix = 0; ix < W; ix++) {
+            int j, k;
+            double fv, fu;
+            if (!scan_coords(n, S, fov, depth, W, H, x0, x1, z0, z1, ix, iz, &j, &k, &fv, &fu)) continue;
+            double g = gout[(long)iz * W + ix];
+            double *r0 = gimg + (long)j * S, *r1 = gimg + (long)(j + 1) * S;
+            r0[k] += (1.0 - fv) * (1.0 - fu) * g;
+            r1[k] += fv * (1.0 - fu) * g;
+            r0[k + 1] += (1.0 - fv) * fu * g;
+            r1[k + 1] += fv * fu * g;
+        }
+    return 0;
+}
