@@ -249,6 +249,44 @@ int diffus_render_batch(const void *vol, const diffus_volume_desc *vd, const flo
                         float *grad_poses, uint32_t *status, void *workspace, size_t ws_bytes,
                         const diffus_trace *trace, diffus_stream_t stream);
 
+/* ------------------------------------------------------------ scan conversion
+ *
+ * The fan-shaped display image (Section 2.4, Fig. 3): a polar image
+ * [n_rays][S] (row j = beam angle theta_j of the fan's inclusive linspace,
+ * column k = echo row k at depth (k+1) ds, ds = depth/S) is resampled onto a
+ * W x H Cartesian grid of the imaging plane (x lateral, z axial, apex at the
+ * origin).  Pixel (ix, iz) has centre x = x0 + (ix + 1/2)(x1 - x0)/W,
+ * z = z0 + (iz + 1/2)(z1 - z0)/H; with rho = |(x, z)|, theta = atan2(x, z),
+ * v = (theta + fov/2)(n - 1)/fov and u = rho/ds - 1 its value is the bilinear
+ * interpolation of the polar image at (ray v, row u) inside the fan
+ * (0 <= v <= n-1, 0 <= u <= S-1) and 0 outside.  Output layout [H][W]. */
+typedef struct {
+    int32_t width, height;       /* W, H pixels (W * H <= 2^30) */
+    double x0, x1, z0, z1;       /* mm, x0 < x1, z0 < z1 */
+} diffus_scan_grid;
+
+/* Size of the scan plan of one fan and grid (0 if either is invalid; the
+ * fan needs n_rays >= 2 and n_samples >= 2). */
+size_t diffus_scan_plan_bytes(const diffus_fan *fan, const diffus_scan_grid *grid);
+
+/* Host-only planning in FP64: every display pixel's bilinear tap and the
+ * transposed map (per polar pixel, its display pixels and weights in pixel
+ * order) into plan_host (host, diffus_scan_plan_bytes bytes).  The caller
+ * copies the plan to device memory (256-byte aligned) once. */
+int diffus_scan_plan(const diffus_fan *fan, const diffus_scan_grid *grid, void *plan_host, size_t plan_bytes);
+
+/* Scan-converts `count` polar images of the plan's fan: images (device
+ * float [count][n_rays][S]) -> out (device float [count][H][W]). */
+int diffus_scan_convert(const float *images, int32_t count, const void *plan_host, const void *plan_dev, float *out,
+                        diffus_stream_t stream);
+
+/* Adjoint (transpose) of diffus_scan_convert: grad_out (device float
+ * [count][H][W]) -> grad_images (device float [count][n_rays][S],
+ * overwritten).  Atomic-free: every polar pixel sums its display pixels in
+ * a fixed order. */
+int diffus_scan_convert_bwd(const float *grad_out, int32_t count, const void *plan_host, const void *plan_dev,
+                            float *grad_images, diffus_stream_t stream);
+
 /* ------------------------------------------------------------------ misc */
 
 /* Philox4x32-10 (Salmon et al., SC'11), the generator behind the speckle of

@@ -45,6 +45,11 @@ class ScheduleDesc(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class ScanGridDesc(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("x0", C.c_double), ("x1", C.c_double),
+                ("z0", C.c_double), ("z1", C.c_double)]
+
+
 class TraceDesc(C.Structure):
     _fields_ = [("event", C.c_void_p * 10)]
 
@@ -87,6 +92,11 @@ def load(build_if_missing: bool = True):
         lib.diffus_version.restype = C.c_int
         lib.diffus_philox.argtypes = [vp, C.c_int64, C.c_uint64, vp, vp]
         lib.diffus_render_fwd_noalloc.argtypes = [vp, p(VolumeDesc), vp, p(FanDesc), p(ParamsDesc), vp, vp, vp, vp]
+        lib.diffus_scan_plan_bytes.argtypes = [p(FanDesc), p(ScanGridDesc)]
+        lib.diffus_scan_plan_bytes.restype = C.c_size_t
+        lib.diffus_scan_plan.argtypes = [p(FanDesc), p(ScanGridDesc), vp, C.c_size_t]
+        lib.diffus_scan_convert.argtypes = [vp, C.c_int32, vp, vp, vp, vp]
+        lib.diffus_scan_convert_bwd.argtypes = [vp, C.c_int32, vp, vp, vp, vp]
         _lib = lib
         return lib
 
@@ -262,3 +272,40 @@ def philox(ctr: torch.Tensor, key: int, out=None, stream=None):
 
 def version() -> int:
     return int(load().diffus_version())
+
+
+# ------------------------------------------------------------ scan conversion
+
+def scan_plan(fan, grid):
+    """diffus_scan_plan (host): grid = (W, H, x0, x1, z0, z1); returns the
+    plan bytes as a uint8 CPU tensor."""
+    lib = load()
+    fd = fan_desc(fan)
+    gd = ScanGridDesc(int(grid[0]), int(grid[1]), *[float(v) for v in grid[2:]])
+    nbytes = lib.diffus_scan_plan_bytes(C.byref(fd), C.byref(gd))
+    if nbytes == 0:
+        raise DiffusError("invalid fan or display grid for scan conversion")
+    plan = torch.empty(int(nbytes), dtype=torch.uint8)
+    _check(lib.diffus_scan_plan(C.byref(fd), C.byref(gd), C.c_void_p(plan.data_ptr()), int(nbytes)),
+           "diffus_scan_plan")
+    return plan
+
+
+def scan_convert(images, plan_host, plan_dev, out, stream=None):
+    """diffus_scan_convert on device tensors: images [count][n][S] -> out [count][H][W]."""
+    _require_cuda(images, out, plan_dev)
+    count = images.shape[0] if images.dim() == 3 else 1
+    rc = load().diffus_scan_convert(_ptr(images), count, C.c_void_p(plan_host.data_ptr()), _ptr(plan_dev), _ptr(out),
+                                    _stream(stream))
+    _check(rc, "diffus_scan_convert")
+    return out
+
+
+def scan_convert_bwd(grad_out, plan_host, plan_dev, grad_images, stream=None):
+    """diffus_scan_convert_bwd: grad_out [count][H][W] -> grad_images [count][n][S]."""
+    _require_cuda(grad_out, grad_images, plan_dev)
+    count = grad_out.shape[0] if grad_out.dim() == 3 else 1
+    rc = load().diffus_scan_convert_bwd(_ptr(grad_out), count, C.c_void_p(plan_host.data_ptr()), _ptr(plan_dev),
+                                        _ptr(grad_images), _stream(stream))
+    _check(rc, "diffus_scan_convert_bwd")
+    return grad_images

@@ -138,3 +138,51 @@ def autotune(volume, spacing, origin, fans, params, poses, grad_images=None, can
             best, best_t = sched, t
         del r
     return best, timings
+
+
+def fan_grid(fan, width, height):
+    """Default display grid of a fan: x over [-depth sin(fov/2), depth sin(fov/2)]
+    (fov <= 180 degrees), z over [0, depth]; (W, H, x0, x1, z0, z1)."""
+    import math
+    half = float(fan.depth) * math.sin(min(0.5 * float(fan.fov), 0.5 * math.pi))
+    return (int(width), int(height), -half, half, 0.0, float(fan.depth))
+
+
+class _ScanConvert(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, images, conv):
+        x = images.detach().contiguous().float()
+        squeeze = x.dim() == 2
+        if squeeze:
+            x = x.unsqueeze(0)
+        out = torch.empty((x.shape[0], conv.height, conv.width), dtype=torch.float32, device=x.device)
+        B.scan_convert(x, conv.plan_host, conv.plan_dev, out)
+        ctx.conv, ctx.squeeze, ctx.shape = conv, squeeze, x.shape
+        return out[0] if squeeze else out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g = grad_out.contiguous().float()
+        if ctx.squeeze:
+            g = g.unsqueeze(0)
+        gi = torch.empty(ctx.shape, dtype=torch.float32, device=g.device)
+        B.scan_convert_bwd(g, ctx.conv.plan_host, ctx.conv.plan_dev, gi)
+        return (gi[0] if ctx.squeeze else gi), None
+
+
+class ScanConverter:
+    """Bilinear scan conversion of polar images of one fan onto a Cartesian
+    display grid (the fan-shaped B-mode image), differentiable through
+    diffus_scan_convert_bwd.  The plan is built once on the host."""
+
+    def __init__(self, fan, width, height, grid=None, device="cuda"):
+        self.fan = fan
+        self.grid = tuple(grid) if grid is not None else fan_grid(fan, width, height)
+        self.width, self.height = int(self.grid[0]), int(self.grid[1])
+        plan = B.scan_plan(fan, self.grid)
+        self.plan_host = plan.pin_memory() if torch.cuda.is_available() else plan
+        self.plan_dev = plan.to(device)
+
+    def __call__(self, images):
+        """images [n_rays][S] or [count][n_rays][S] -> [H][W] or [count][H][W]."""
+        return _ScanConvert.apply(images, self)
