@@ -43,7 +43,7 @@ class _Fan(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("mode", C.c_int32), ("speckle", C.c_int32),
                 ("Ar", C.c_double), ("pr", C.c_double), ("Ag", C.c_double), ("pg", C.c_double),
-                ("Lr", C.c_int32), ("gshift", C.c_int32), ("blur", C.c_int32), ("pad_", C.c_int32),
+                ("Lr", C.c_int32), ("gshift", C.c_int32), ("blur", C.c_int32), ("atten", C.c_int32),
                 ("sigma0", C.c_double), ("sigma1", C.c_double)]
 
 
@@ -113,7 +113,7 @@ def _fan(f) -> _Fan:
 
 def _params(p) -> _Params:
     return _Params(int(p.seed) & (2**64 - 1), int(p.mode), int(p.speckle), float(p.Ar), float(p.pr),
-                   float(p.Ag), float(p.pg), int(p.Lr), int(p.gshift), int(p.blur), 0,
+                   float(p.Ag), float(p.pg), int(p.Lr), int(p.gshift), int(p.blur), int(getattr(p, "atten", 0)),
                    float(p.sigma0), float(p.sigma1))
 
 

@@ -65,9 +65,20 @@ typedef struct {
     int32_t Lr;                 /* radial correlation half-length (samples) */
     int32_t gshift;             /* log2 grain length in the shallowest band */
     int32_t blur;               /* 0 off, 1 on */
-    int32_t pad_;
+    int32_t atten;              /* 0: attenuation inside Eq. 4; 1: lossless system and depth gain */
     double sigma0, sigma1;      /* lateral blur width (rays) at surface / growth */
 } or_params;
+
+/* The second reading of "uniform attenuation" (Section 2.1): with atten = 1
+ * the depth systems are solved with a = 1 and echo row k is multiplied by
+ * the round-trip gain a^(2(k+1)) of its depth (k+1) ds.  Single echoes are the
+ * same in both readings; multiply reflected paths are weighted differently. */
+double or_attenuation(const or_fan *fan);
+static double system_a(const or_params *p, const or_fan *fan) { return p->atten ? 1.0 : or_attenuation(fan); }
+static double depth_gain(const or_params *p, const or_fan *fan, int k)
+{
+    return p->atten ? pow(or_attenuation(fan), 2.0 * (double)(k + 1)) : 1.0;
+}
 
 int or_num_threads(void)
 {
@@ -627,11 +638,11 @@ static int ray_echo(const float *vol, const or_grid *g, const double pose[6], co
     double *m = malloc(sizeof(double) * (size_t)S);
     or_ray_positions(pose, fan, j, pos);
     for (int k = 0; k <= S; k++) Z[k] = or_trilinear(vol, g, pos + 3 * k, NULL);
-    int rc = or_profile(Z, S, or_attenuation(fan), p->mode, 0, d0, det);
+    int rc = or_profile(Z, S, system_a(p, fan), p->mode, 0, d0, det);
     or_speckle(p, pose_ctr, j, S, m);
     int fb = S + 1;
     for (int k = S; k >= 1; k--) if (!(det[k] >= 1e-6)) fb = k;
-    for (int k = 0; k < S; k++) y[k] = m[k] * (d0[k + 1] - d0[k]);
+    for (int k = 0; k < S; k++) y[k] = m[k] * depth_gain(p, fan, k) * (d0[k + 1] - d0[k]);
     *first = fb;
     if (det_out) memcpy(det_out, det, sizeof(double) * (size_t)(S + 1));
     free(pos); free(Z); free(d0); free(det); free(m);
@@ -690,7 +701,7 @@ int or_render_grad(const float *vol, const or_grid *g, const double pose[6], con
                    const or_params *p, uint32_t pose_ctr, const double *gimg, double *gvol, double gpose[6])
 {
     int n = fan->n_rays, S = fan->n_samples;
-    double a = or_attenuation(fan);
+    double a = system_a(p, fan);
     double *gy = malloc(sizeof(double) * (size_t)n * S);
     or_blur_T(p, gimg, n, S, gy);
     double *gZall = malloc(sizeof(double) * (size_t)n * (S + 1));
@@ -726,7 +737,7 @@ int or_render_grad(const float *vol, const or_grid *g, const double pose[6], con
         or_speckle(p, pose_ctr, j, S, m);
         /* y[k] = m[k] (d0[k+1] - d0[k]) */
         for (int k = 0; k < S; k++) {
-            double gI = m[k] * gy[(long)j * S + k];
+            double gI = m[k] * depth_gain(p, fan, k) * gy[(long)j * S + k];
             gd0[k + 1] += gI;
             gd0[k] -= gI;
         }

@@ -71,6 +71,7 @@ class Params:
     sigma0: float = 0.25
     sigma1: float = 2.0
     refine: int = 0
+    atten: int = 0      # 0: attenuation inside Eq. 4; 1: lossless system times the depth gain
 
     def with_(self, **kw):
         return replace(self, **kw)

@@ -435,3 +435,52 @@ def test_render_gradient_matches_finite_differences():
             dp[idx] += np.float32(hv); dm[idx] -= np.float32(hv)
             fd = (loss(v=I.Volume(dp, vol.spacing, vol.origin)) - loss(v=I.Volume(dm, vol.spacing, vol.origin))) / (2 * hv)
             assert abs(fd - gvol[idx]) < 2e-5 * max(1.0, abs(fd)), (idx, fd, gvol[idx])
+
+
+def _layered_ray(layers, S, ds=1.0):
+    """One straight-down ray whose sample k sits exactly on voxel centre k of
+    a volume layered along z: returns (vol, pose, fan) with Z_k = layers[k]."""
+    z = np.asarray(layers, np.float32)
+    vol = I.Volume(np.broadcast_to(z[:, None, None], (z.size, 3, 3)).copy(), (ds, ds, ds), (0.0, 0.0, 0.0))
+    pose = np.array([1.0, 1.0, -0.5 * ds, 0.0, 0.0, 0.0])     # sample k at z = k ds
+    fan = I.Fan(1, S, 0.0, S * ds, 5.0, 0.5)
+    return vol, pose, fan
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_depth_gain_reading_two_layer_equals_in_system(mode):
+    # one interface: a single echo R a^{2(m+1)} at row m in both attenuation readings
+    S, m = 20, 7
+    z1, z2 = float(np.float32(1.5)), float(np.float32(2.6))      # the volume stores float32
+    vol, pose, fan = _layered_ray([z1] * (m + 1) + [z2] * (S - m), S)
+    a = oracle.attenuation(fan)
+    r = (z2 - z1) / (z1 + z2)
+    expect = np.zeros(S)
+    expect[m] = (abs(r) if mode == 0 else r) * a ** (2 * (m + 1))
+    for atten in (0, 1):
+        img, _ = oracle.render(vol, pose, fan, I.Params(mode=mode, speckle=0, blur=0, atten=atten))
+        np.testing.assert_allclose(img[0], expect, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_depth_gain_reading_three_layer_airy(mode):
+    # two interfaces at rows m and m+L: with the depth gain the second echo is
+    # a^{2(m+L+1)} T1 T1' R2 / (1 - R1' R2) (lossless multiple reflections),
+    # inside the system it is a^{2(m+L+1)} T1 T1' R2 / (1 - R1' a^{2L} R2)
+    S, m, L = 24, 5, 6
+    z1, z2, z3 = (float(np.float32(v)) for v in (1.4, 2.9, 1.7))
+    vol, pose, fan = _layered_ray([z1] * (m + 1) + [z2] * L + [z3] * (S - m - L), S)
+    a = oracle.attenuation(fan)
+
+    def co(x, y):
+        r = (y - x) / (x + y)
+        return (abs(r), abs(r)) if mode == 0 else (r, -r), 2 * y / (x + y), 2 * x / (x + y)
+
+    (R1, R1p), T1, T1p = co(z1, z2)
+    (R2, _), _, _ = co(z2, z3)
+    g = a ** (2 * (m + L + 1))
+    gain_img, _ = oracle.render(vol, pose, fan, I.Params(mode=mode, speckle=0, blur=0, atten=1))
+    sys_img, _ = oracle.render(vol, pose, fan, I.Params(mode=mode, speckle=0, blur=0, atten=0))
+    assert abs(gain_img[0, m + L] - g * T1 * T1p * R2 / (1 - R1p * R2)) < 1e-14
+    assert abs(sys_img[0, m + L] - g * T1 * T1p * R2 / (1 - R1p * a ** (2 * L) * R2)) < 1e-14
+    assert abs(gain_img[0, m + L] - sys_img[0, m + L]) > 1e-6
