@@ -110,7 +110,11 @@ typedef struct {
  *    FP64 (coefficients recomputed in FP64 from the same samples), the
  *    error recurrence is solved in FP32 and the echoes use the corrected
  *    states.  Any volume dtype, single-pose and batched forward; the
- *    adjoint stays FP32. */
+ *    adjoint stays FP32.
+ *  atten (the two readings of "uniform attenuation", Section 2.1): 0 puts
+ *    the amplitude factor a = 10^(-alpha f ds / 20) of every sample cell
+ *    inside the rows of Eq. 4 (default); 1 solves the depth systems with
+ *    a = 1 and multiplies echo row k by the round-trip gain a^(2(k+1)). */
 typedef struct {
     uint64_t seed;
     int32_t mode;
@@ -122,7 +126,7 @@ typedef struct {
     int32_t refine;             /* 0/1 */
     double sigma0, sigma1;      /* >= 0 */
     uint32_t pose_ctr;          /* Philox pose word for pose 0 of the call */
-    uint32_t reserved;
+    int32_t atten;              /* 0: attenuation inside Eq. 4; 1: depth gain (see above) */
 } diffus_params;
 
 /* ------------------------------------------------------------ single pose */

@@ -37,7 +37,7 @@ class ParamsDesc(C.Structure):
                 ("Ar", C.c_double), ("pr", C.c_double), ("Ag", C.c_double), ("pg", C.c_double),
                 ("Lr", C.c_int32), ("gshift", C.c_int32), ("blur", C.c_int32), ("refine", C.c_int32),
                 ("sigma0", C.c_double), ("sigma1", C.c_double), ("pose_ctr", C.c_uint32),
-                ("reserved", C.c_uint32)]
+                ("atten", C.c_int32)]
 
 
 class ScheduleDesc(C.Structure):
@@ -130,7 +130,7 @@ def params_desc(p, pose_ctr: int = 0) -> ParamsDesc:
     return ParamsDesc(int(p.seed) & (2**64 - 1), int(p.mode), int(p.speckle), float(p.Ar), float(p.pr),
                       float(p.Ag), float(p.pg), int(p.Lr), int(p.gshift), int(p.blur),
                       int(getattr(p, "refine", 0)), float(p.sigma0), float(p.sigma1), int(pose_ctr) & 0xFFFFFFFF,
-                      0)
+                      int(getattr(p, "atten", 0)))
 
 
 def _ptr(t):

@@ -7,6 +7,7 @@
 // tiles.  diffus_render_batch then launches only kernels and async memsets,
 // so a whole forward+backward step can be captured in one CUDA graph.
 #include <algorithm>
+#include <cmath>
 #include <numeric>
 #include <vector>
 
@@ -29,6 +30,8 @@ struct PlanPose {
     int32_t W;
     int64_t img_off;
     double a2d;
+    float l2_hi, l2_lo;      // log2(a^2) split (depth-gain reading)
+    int32_t pad;
 };
 
 struct BlurTile {                 // one 32-row strip of one pose image
@@ -55,7 +58,7 @@ T *at_mut(void *base, int64_t off) { return (T *)((char *)base + off); }
 
 uint64_t params_fingerprint(const diffus_params *p)
 {
-    // fields that change the plan (blur width)
+    // fields that change the plan (blur width) or its workspace (depth gain)
     uint64_t h = 1469598103934665603ull;
     auto mix = [&](const void *d, size_t n) {
         const unsigned char *c = (const unsigned char *)d;
@@ -64,6 +67,7 @@ uint64_t params_fingerprint(const diffus_params *p)
     mix(&p->blur, sizeof p->blur);
     mix(&p->sigma0, sizeof p->sigma0);
     mix(&p->sigma1, sizeof p->sigma1);
+    mix(&p->atten, sizeof p->atten);
     return h;
 }
 
@@ -114,7 +118,8 @@ struct BatchLayout {
     size_t fwd_bytes, bytes;
 };
 
-BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc *vd, bool blur, bool speckle)
+BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc *vd, bool blur, bool speckle,
+                         bool atten)
 {
     Carve c(ws);
     BatchLayout L;
@@ -122,7 +127,7 @@ BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc
     L.counter = c.take<unsigned>(4);
     L.y = blur ? c.take<float>((size_t)H.total_img) : nullptr;
     L.fwd_bytes = c.used;
-    L.gy = blur ? c.take<float>((size_t)H.total_img) : nullptr;
+    L.gy = (blur || atten) ? c.take<float>((size_t)H.total_img) : nullptr;
     L.mbuf = speckle ? c.take<float>((size_t)H.total_img) : nullptr;
     L.gz = c.take<float>((size_t)H.total_gz);
     L.part = c.take<double>(6 * (size_t)H.total_rays);
@@ -172,8 +177,10 @@ __global__ void __launch_bounds__(WARPS * 32, REFINE ? 1 : kFwdThreadsPerSM / (W
         const int r = B.order[q];
         RayGeo rg = geo[r];
         MarchArgs Ap = A;
-        Ap.a2 = B.pose[rg.pose].a2;
-        Ap.a2d = B.pose[rg.pose].a2d;
+        if (!A.atten) {   // the depth-gain reading keeps a2 = 1 (lossless systems)
+            Ap.a2 = B.pose[rg.pose].a2;
+            Ap.a2d = B.pose[rg.pose].a2d;
+        }
         RayOut o{out + B.row_off[r], valid ? valid + r : nullptr, status, ckpt ? ckpt + B.ck_off[r] : nullptr,
                  mbuf ? mbuf + B.row_off[r] : nullptr};
         march_fwd_ray<T, REFINE>(vol, Ap, rg, o, buf[w], REFINE ? dbuf[w] : nullptr);
@@ -199,11 +206,26 @@ __global__ void __launch_bounds__(WARPS * 32, kBwdThreadsPerSM / (WARPS * 32)) k
         const int r = B.order[q];
         RayGeo rg = geo[r];
         MarchArgs Ap = A;
-        Ap.a2 = B.pose[rg.pose].a2;
-        Ap.a2d = B.pose[rg.pose].a2d;
+        if (!A.atten) {   // the depth-gain reading keeps a2 = 1 (lossless systems)
+            Ap.a2 = B.pose[rg.pose].a2;
+            Ap.a2d = B.pose[rg.pose].a2d;
+        }
         march_bwd_ray<T>(vol, Ap, rg, gy + B.row_off[r], gz + B.gz_off[r], part + 6 * (size_t)r,
                          ckpt + B.ck_off[r], sm[w], true, mbuf ? mbuf + B.row_off[r] : nullptr);
         __syncwarp();
+    }
+}
+
+// Depth-gain row pass over all rays of the batch (one warp per ray):
+// out[row + k] = in[row + k] gain_p(k) (in and out may alias).
+__global__ void k_batch_row_gain(const float *in, float *out, BatchDev B)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < B.total_rays; r += nw) {
+        const PlanPose pp = B.pose[B.ray_pose[r]];
+        const int64_t off = B.row_off[r];
+        for (int k = lane; k < pp.S; k += 32) out[off + k] = in[off + k] * depth_gain(pp.l2_hi, pp.l2_lo, k);
     }
 }
 
@@ -394,7 +416,9 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     for (int p = 0; p < P; p++) {
         const diffus_fan &f = fans[p];
         double a = attenuation_a(&f);
-        pp[p] = PlanPose{f.n_rays, f.n_samples, f.fov_rad, f.depth_mm, (float)(a * a), H.blurW, img, a * a};
+        float hi, lo;
+        gain_l2(a, hi, lo);
+        pp[p] = PlanPose{f.n_rays, f.n_samples, f.fov_rad, f.depth_mm, (float)(a * a), H.blurW, img, a * a, hi, lo, 0};
         depth[p] = f.depth_mm;
         ray0[p] = (int32_t)r;
         img_offsets[p] = img;
@@ -422,7 +446,7 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     // blur strips of the widest poses first (a strip's work grows with n_rays)
     std::stable_sort(tiles, tiles + n_tiles, [](const BlurTile &x, const BlurTile &y) { return x.n_rays > y.n_rays; });
 
-    BatchLayout L = batch_layout(nullptr, H, vd, prm->blur != 0, prm->speckle != 0);
+    BatchLayout L = batch_layout(nullptr, H, vd, prm->blur != 0, prm->speckle != 0, prm->atten != 0);
     if (ws_fwd) *ws_fwd = L.fwd_bytes;
     if (ws_bwd) *ws_bwd = L.bytes;
     return DIFFUS_OK;
@@ -446,7 +470,7 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
         ((uintptr_t)workspace) % 256 || ((uintptr_t)plan_dev) % 256)
         return DIFFUS_E_ALIGN;
     const bool bwd = grad_images != nullptr;
-    BatchLayout L = batch_layout(workspace, H, vd, prm->blur != 0, prm->speckle != 0);
+    BatchLayout L = batch_layout(workspace, H, vd, prm->blur != 0, prm->speckle != 0, prm->atten != 0);
     if (ws_bytes < (bwd ? L.bytes : L.fwd_bytes)) return DIFFUS_E_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -488,6 +512,8 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
         rc = launch_fwd_w<unsigned short>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0,
                                           ck, mb, grid, prm->refine != 0, s);
     if (rc) return rc;
+    const int rgrid = (int)std::min<int64_t>((H.total_rays + 7) / 8, (int64_t)sm_count() * 16);
+    if (prm->atten) k_batch_row_gain<<<rgrid, 256, 0, s>>>(march_out, march_out, B);
     mark(DIFFUS_TR_BLUR);
     BlurArgs bl{(float)prm->sigma0, (float)prm->sigma1, H.blurW};
     const int tgrid = (int)std::min<int64_t>((H.n_tiles + kBlurWarps - 1) / kBlurWarps, (int64_t)sm_count() * 16);
@@ -504,6 +530,10 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     const float *gy = grad_images;
     if (prm->blur) {
         launch_batch_blur<true>(grad_images, L.gy, dpose, dtiles, H.n_tiles, bl, tgrid, s);
+        gy = L.gy;
+    }
+    if (prm->atten) {   // the depth gain is a diagonal row factor: its adjoint is itself
+        k_batch_row_gain<<<rgrid, 256, 0, s>>>(gy, L.gy, B);
         gy = L.gy;
     }
     mark(DIFFUS_TR_MARCH_BWD);

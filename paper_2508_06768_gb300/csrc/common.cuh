@@ -122,6 +122,28 @@ __device__ __forceinline__ void sample_z(const T *__restrict__ vol, const VolGeo
     }
 }
 
+// Round-trip depth gain a^(2(k+1)) = 2^((k+1) l2) of echo row k under the
+// depth-gain reading of attenuation, l2 = log2(a^2) = l2_hi + l2_lo.  The
+// exponent's rounding is carried separately (exact product residual by fma
+// plus the low part of l2), so the gain is good to a few ulp even 4096 rows
+// deep.
+__device__ __forceinline__ float depth_gain(float l2_hi, float l2_lo, int k)
+{
+    const float kf = (float)(k + 1);
+    const float p = kf * l2_hi;
+    const float e = fmaf(kf, l2_hi, -p) + kf * l2_lo;
+    return exp2f(p) * fmaf(e, 0.6931471805599453f, 1.0f);
+}
+
+// Row gain pass of one pose image [n][S]: out[j][k] = in[j][k] gain(k)
+// (in and out may alias).
+__global__ static void k_row_gain(const float *in, float *out, int n, int S, float l2_hi, float l2_lo)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n * S) return;
+    out[i] = in[i] * depth_gain(l2_hi, l2_lo, (int)(i % S));
+}
+
 // Reciprocal on the special-function unit (<= 2 ulp): ample for the 1e-5
 // tolerance, and far cheaper than the IEEE-rounded one.
 __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }

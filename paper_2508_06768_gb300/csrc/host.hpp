@@ -49,6 +49,7 @@ inline int check_params(const diffus_params *p)
     if (p->speckle != 0 && p->speckle != 1) return DIFFUS_E_PARAM;
     if (p->blur != 0 && p->blur != 1) return DIFFUS_E_PARAM;
     if (p->refine != 0 && p->refine != 1) return DIFFUS_E_PARAM;
+    if (p->atten != 0 && p->atten != 1) return DIFFUS_E_PARAM;
     if (p->Lr < 0 || p->Lr > 4) return DIFFUS_E_PARAM;
     if (p->gshift < 0 || p->gshift > 16) return DIFFUS_E_PARAM;
     double v[6] = {p->Ar, p->pr, p->Ag, p->pg, p->sigma0, p->sigma1};
@@ -64,6 +65,14 @@ inline int blur_halfwidth(const diffus_params *p)
     if (!p->blur) return 0;
     double s = p->sigma0 + p->sigma1;
     return s > 0.0 ? (int)ceil(3.0 * s) : 0;
+}
+
+// log2(a^2) of a fan split into two floats (depth-gain reading).
+inline void gain_l2(double a, float &hi, float &lo)
+{
+    const double l2 = std::log2(a * a);
+    hi = (float)l2;
+    lo = (float)(l2 - (double)hi);
 }
 
 inline double attenuation_a(const diffus_fan *f)

@@ -23,9 +23,10 @@ namespace dfs {
 
 struct MarchArgs {
     VolGeo g;
-    float a2;         // a^2, round-trip amplitude factor of one cell
+    float a2;         // a^2 inside the depth systems (1 with the depth-gain reading)
     int mode;
-    double a2d;       // a^2 in FP64 (residual of the refinement pass)
+    double a2d;       // the same in FP64 (residual of the refinement pass)
+    int atten;        // 1: depth-gain reading (lossless systems; the gain is a separate row pass)
     Speckle sp;
 };
 

@@ -86,7 +86,7 @@ static BwdLayout bwd_layout(void *ws, const diffus_volume_desc *vd, const diffus
     size_t n = (size_t)fan->n_rays, S = (size_t)fan->n_samples;
     size_t nseg = (S + kSeg - 1) / kSeg;
     L.geo = c.take<RayGeo>(n);
-    L.gy = prm->blur ? c.take<float>(n * S) : nullptr;
+    L.gy = (prm->blur || prm->atten) ? c.take<float>(n * S) : nullptr;
     L.gz = c.take<float>(n * (S + 1));
     L.part = c.take<double>(6 * n);
     L.ckpt = c.take<float4>(n * nseg);
@@ -129,6 +129,13 @@ extern "C" int diffus_render_bwd(const void *vol, const diffus_volume_desc *vd, 
     const float *gy = grad_image;
     if (prm->blur) {
         if ((rc = launch_blur(grad_image, L.gy, n, S, prm, true, s))) return rc;
+        gy = L.gy;
+    }
+    if (prm->atten) {   // the depth gain is a diagonal row factor: its adjoint is itself
+        float hi, lo;
+        gain_l2(attenuation_a(fan), hi, lo);
+        const int64_t ne = (int64_t)n * S;
+        k_row_gain<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(gy, L.gy, (int)n, (int)S, hi, lo);
         gy = L.gy;
     }
     MarchArgs A = make_march_args(vd, fan, prm);

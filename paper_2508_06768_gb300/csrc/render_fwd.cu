@@ -1,4 +1,6 @@
 // Single-pose forward entry point: ray setup -> warp-per-ray march -> blur.
+#include <cmath>
+
 #include "host.hpp"
 
 using namespace dfs;
@@ -35,8 +37,10 @@ MarchArgs make_march_args(const diffus_volume_desc *vd, const diffus_fan *fan, c
     MarchArgs A;
     A.g = make_volgeo(vd);
     double a = attenuation_a(fan);
-    A.a2 = (float)(a * a);
-    A.a2d = a * a;
+    A.atten = prm->atten;
+    // the depth-gain reading solves lossless systems (its gain is a row pass)
+    A.a2 = prm->atten ? 1.0f : (float)(a * a);
+    A.a2d = prm->atten ? 1.0 : a * a;
     A.mode = prm->mode;
     A.sp = make_speckle(prm);
     return A;
@@ -122,6 +126,13 @@ extern "C" int diffus_render_fwd(const void *vol, const diffus_volume_desc *vd, 
     if (status && cudaMemsetAsync(status, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
     float *march_out = prm->blur ? L.y : image;
     if ((rc = launch_fwd_march(vol, vd, pose, fan, prm, L.geo, march_out, ray_valid, status, s))) return rc;
+    if (prm->atten) {
+        float hi, lo;
+        gain_l2(attenuation_a(fan), hi, lo);
+        const int64_t ne = (int64_t)fan->n_rays * fan->n_samples;
+        k_row_gain<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(march_out, march_out, fan->n_rays, fan->n_samples, hi,
+                                                                lo);
+    }
     if (prm->blur) rc = launch_blur(L.y, image, fan->n_rays, fan->n_samples, prm, false, s);
     return rc;
 }
