@@ -291,6 +291,20 @@ int diffus_scan_convert(const float *images, int32_t count, const void *plan_hos
 int diffus_scan_convert_bwd(const float *grad_out, int32_t count, const void *plan_host, const void *plan_dev,
                             float *grad_images, diffus_stream_t stream);
 
+/* ------------------------------------------------------------- CT pre-pass
+ *
+ * Hounsfield units to acoustic impedance for CT volumes (the impedance
+ * volume Z of Section 2.2 from a CT scan instead of the MRI network, which
+ * is out of scope): z[v] = f(hu[v]) with f the piecewise-linear map through
+ * the user's calibration breakpoints (hu_pts[i], z_pts[i]), i < m <= 64,
+ * hu_pts strictly increasing integers, clamped to z_pts[0] below hu_pts[0]
+ * and to z_pts[m-1] above hu_pts[m-1].  hu: device int16 [n]; hu_pts and
+ * z_pts: host double [m]; z_out: device [n] of out_dtype (DIFFUS_F32, or
+ * DIFFUS_BF16 rounded to nearest even), e.g. the volume the renderer then
+ * samples.  The paper gives no table. */
+int diffus_hu_to_z(const int16_t *hu, int64_t n, const double *hu_pts, const double *z_pts, int32_t m, void *z_out,
+                   int32_t out_dtype, diffus_stream_t stream);
+
 /* ------------------------------------------------------------------ misc */
 
 /* Philox4x32-10 (Salmon et al., SC'11), the generator behind the speckle of

@@ -88,6 +88,7 @@ def _load():
                   C.c_double, C.c_double, dp]
             lib.or_scan_convert.argtypes = sc
             lib.or_scan_convert_T.argtypes = sc
+            lib.or_hu_to_z.argtypes = [C.c_void_p, C.c_long, dp, dp, C.c_int, dp]
             _lib = lib
     return _lib
 
@@ -318,3 +319,15 @@ def scan_convert_T(gout, fan, n, S, grid):
     if rc:
         raise ValueError("scan conversion needs n_rays >= 2, n_samples >= 2 and a positive field of view")
     return g
+
+
+def hu_to_z(hu, hu_pts, z_pts):
+    """Piecewise-linear HU -> impedance map of an int16 array (clamped to the
+    end values outside the table)."""
+    h = np.ascontiguousarray(np.asarray(hu, dtype=np.int16))
+    hp, zp = _f64(hu_pts), _f64(z_pts)
+    z = np.zeros(h.shape)
+    rc = _load().or_hu_to_z(h.ctypes.data, h.size, _dp(hp), _dp(zp), hp.size, _dp(z))
+    if rc:
+        raise ValueError("the HU table needs >= 1 breakpoint with strictly increasing HU")
+    return z

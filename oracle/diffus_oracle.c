@@ -852,3 +852,26 @@ int or_scan_convert_T(const double *gout, int n, int S, double fov, double depth
         }
     return 0;
 }
+
+/* ------------------------------------------------------------------
+ * CT Hounsfield units to acoustic impedance (a pre-pass for CT volumes; the
+ * calibration table is the user's, the paper gives none).  The table holds
+ * m >= 1 breakpoints (hu_i, z_i) with strictly increasing hu_i; a value
+ * below hu_0 maps to z_0, above hu_{m-1} to z_{m-1}, and in between to the
+ * straight line through the two breakpoints around it. */
+int or_hu_to_z(const int16_t *hu, long n, const double *hu_pts, const double *z_pts, int m, double *z)
+{
+    if (m < 1) return -1;
+    for (int i = 1; i < m; i++)
+        if (!(hu_pts[i] > hu_pts[i - 1])) return -1;
+    for (long v = 0; v < n; v++) {
+        double h = (double)hu[v];
+        if (h <= hu_pts[0]) { z[v] = z_pts[0]; continue; }
+        if (h >= hu_pts[m - 1]) { z[v] = z_pts[m - 1]; continue; }
+        int i = 0;
+        while (h > hu_pts[i + 1]) i++;
+        double t = (h - hu_pts[i]) / (hu_pts[i + 1] - hu_pts[i]);
+        z[v] = z_pts[i] + t * (z_pts[i + 1] - z_pts[i]);
+    }
+    return 0;
+}

@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
         lib.diffus_version.restype = C.c_int
         lib.diffus_philox.argtypes = [vp, C.c_int64, C.c_uint64, vp, vp]
         lib.diffus_render_fwd_noalloc.argtypes = [vp, p(VolumeDesc), vp, p(FanDesc), p(ParamsDesc), vp, vp, vp, vp]
+        lib.diffus_hu_to_z.argtypes = [vp, C.c_int64, vp, vp, C.c_int32, vp, C.c_int32, vp]
         lib.diffus_scan_plan_bytes.argtypes = [p(FanDesc), p(ScanGridDesc)]
         lib.diffus_scan_plan_bytes.restype = C.c_size_t
         lib.diffus_scan_plan.argtypes = [p(FanDesc), p(ScanGridDesc), vp, C.c_size_t]
@@ -309,3 +310,24 @@ def scan_convert_bwd(grad_out, plan_host, plan_dev, grad_images, stream=None):
                                         _ptr(grad_images), _stream(stream))
     _check(rc, "diffus_scan_convert_bwd")
     return grad_images
+
+
+def hu_to_z(hu, hu_pts, z_pts, dtype=None, out=None, stream=None):
+    """diffus_hu_to_z: int16 CUDA tensor of Hounsfield units -> impedance
+    tensor of the same shape (float32 or bfloat16)."""
+    _require_cuda(hu)
+    if hu.dtype != torch.int16:
+        raise DiffusError("hu must be int16")
+    dtype = dtype or torch.float32
+    if out is None:
+        out = torch.empty(hu.shape, dtype=dtype, device=hu.device)
+    _require_cuda(out)
+    code = 0 if out.dtype == torch.float32 else (1 if out.dtype == torch.bfloat16 else -1)
+    if code < 0:
+        raise DiffusError("output dtype must be float32 or bfloat16")
+    hp = np.ascontiguousarray(np.asarray(hu_pts, dtype=np.float64))
+    zp = np.ascontiguousarray(np.asarray(z_pts, dtype=np.float64))
+    rc = load().diffus_hu_to_z(_ptr(hu), hu.numel(), hp.ctypes.data_as(C.c_void_p), zp.ctypes.data_as(C.c_void_p),
+                               hp.size, _ptr(out), code, _stream(stream))
+    _check(rc, "diffus_hu_to_z")
+    return out
