@@ -151,33 +151,41 @@ __device__ __forceinline__ int ceil_div_fixed(long long num, long long den, int 
     return (int)k;
 }
 
-__device__ __forceinline__ void axis_run(long long X, long long dX, int n, int cap, int &i, float &u, float &v,
-                                         int &steps)
+// Cell index i and upper-corner weight u + v k of one axis at position X
+// (exact in the clamped regions, where v = 0).
+__device__ __forceinline__ void axis_cell(long long X, long long dX, int n, int &i, float &u, float &v)
 {
     const long long top = (long long)(n - 1) << 32;
-    if (X < 0) {                                  // clamped below: weight 0 until X reaches 0
+    if (X < 0) {
         i = 0;
         u = 0.0f;
         v = 0.0f;
-        steps = dX > 0 ? ceil_div_fixed(-X, dX, cap) : cap;
-    } else if (X >= top) {                        // clamped above: weight 1 until X drops below the top
+    } else if (X >= top) {
         i = n - 2;
         u = 1.0f;
         v = 0.0f;
-        steps = dX < 0 ? ceil_div_fixed(X - top + 1, -dX, cap) : cap;
     } else {
-        const long long c = X >> 32;
-        i = (int)c;
+        i = (int)(X >> 32);
         u = __uint_as_float(0x3F800000u | ((unsigned)X >> 9)) - 1.0f;   // 23-bit fraction
         v = (float)dX * 2.3283064365386963e-10f;                        // dX / 2^32
-        if (dX > 0)
-            steps = ceil_div_fixed(((c + 1) << 32) - X, dX, cap);
-        else if (dX < 0)
-            steps = ceil_div_fixed(X - (c << 32) + 1, -dX, cap);
-        else
-            steps = cap;
     }
 }
+
+// Samples from X (inclusive) before the axis's cell or its clamping changes
+// (at most cap): the next crossing of a cell face, of 0 from below or of
+// n-1 from above.
+__device__ __forceinline__ int axis_steps(long long X, long long dX, int n, int cap)
+{
+    const long long top = (long long)(n - 1) << 32;
+    if (X < 0) return dX > 0 ? ceil_div_fixed(-X, dX, cap) : cap;
+    if (X >= top) return dX < 0 ? ceil_div_fixed(X - top + 1, -dX, cap) : cap;
+    const long long c = X >> 32;
+    if (dX > 0) return ceil_div_fixed(((c + 1) << 32) - X, dX, cap);
+    if (dX < 0) return ceil_div_fixed(X - (c << 32) + 1, -dX, cap);
+    return cap;
+}
+
+constexpr int kGStepCap = 1 << 24;   // "no crossing within the run"
 
 // Gather the runs [q0, q1) of one brick (first cell (bx0, by0, bz0)) into
 // this warp's 9^3 accumulator.  Each lane walks one run, one cell at a
@@ -199,6 +207,7 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
     long long X = 0, Y = 0, Z = 0, dX = 0, dY = 0, dZ = 0;
     const float *g = gzbuf;
     int left = 0;                 // samples left in the lane's run
+    int cx = 0, cy = 0, cz = 0;   // samples left before each axis's next crossing (0: recompute)
     uint32_t next = q0;           // next unassigned run (warp-uniform)
     // lane i holds the index of run next + i, loaded one refill ahead
     uint32_t pre = next + lane < q1 ? order[next + lane] : 0u;
@@ -219,6 +228,7 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
                 dZ = run.dZ;
                 g = gzbuf + run.g_off;
                 left = run.len;
+                cx = cy = cz = 0;
             }
             next += __popc(idles);
             pre = next + lane < q1 ? order[next + lane] : 0u;
@@ -228,12 +238,14 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
         int ix = 0, iy = 0, iz = 0, len = 0;
         float ux = 0.0f, vx = 0.0f, uy = 0.0f, vy = 0.0f, uz = 0.0f, vz = 0.0f;
         if (left > 0) {
-            int sx, sy, sz;
-            const int cap = min(left, kGCellCap);
-            axis_run(X, dX, G.nx, cap, ix, ux, vx, sx);
-            axis_run(Y, dY, G.ny, cap, iy, uy, vy, sy);
-            axis_run(Z, dZ, G.nz, cap, iz, uz, vz, sz);
-            len = min(min(sx, sy), min(sz, cap));
+            // DDA countdowns: only an axis that crossed is recomputed
+            if (cx == 0) cx = axis_steps(X, dX, G.nx, kGStepCap);
+            if (cy == 0) cy = axis_steps(Y, dY, G.ny, kGStepCap);
+            if (cz == 0) cz = axis_steps(Z, dZ, G.nz, kGStepCap);
+            axis_cell(X, dX, G.nx, ix, ux, vx);
+            axis_cell(Y, dY, G.ny, iy, uy, vy);
+            axis_cell(Z, dZ, G.nz, iz, uz, vz);
+            len = min(min(cx, cy), min(cz, min(left, kGCellCap)));
         }
         // moments of dL/dZ over the cell's samples
         float M0 = 0.0f, M1 = 0.0f, M2 = 0.0f, M3 = 0.0f;
@@ -278,6 +290,9 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
             Z += (long long)len * dZ;
             g += len;
             left -= len;
+            cx -= len;
+            cy -= len;
+            cz -= len;
         }
         flush_records(has, cell, v, acc, lane, lt);
     }
