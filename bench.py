@@ -136,7 +136,7 @@ BOUND = {"march_fwd": "alu", "march_bwd": "alu", "gather_units": "alu", "blur": 
 # DRAM bytes per ray-sample measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch over the 64-pose prefix of the
 # workload, divided by its ray-samples); absent where the kernel changed since.
-NCU_DRAM_PER_UNIT = {"march_fwd": 6.29, "blur": 6.02, "blur_T": 6.03, "march_bwd": 11.82}
+NCU_DRAM_PER_UNIT = {"march_fwd": 6.31, "blur": 6.03, "blur_T": 6.03, "march_bwd": 11.80, "gather_units": 6.00}
 
 
 def median_pose_order(fans):
