@@ -219,6 +219,13 @@ enum {
 };
 typedef struct {
     void *event[DIFFUS_TR_COUNT];
+    /* Optional input (a cudaEvent_t, or NULL): a forward+backward call makes
+     * its stream wait on this event after the forward and before the first
+     * backward kernel.  A caller that uploads dL/dimage on another stream
+     * records the event after that copy, so the upload overlaps the forward
+     * march; the forward's outputs can likewise be downloaded from the
+     * DIFFUS_TR_FWD_END event on while the backward runs. */
+    void *wait_before_bwd;
 } diffus_trace;
 
 /* Size of the plan blob for P fans (host). */

@@ -51,7 +51,7 @@ class ScanGridDesc(C.Structure):
 
 
 class TraceDesc(C.Structure):
-    _fields_ = [("event", C.c_void_p * 10)]
+    _fields_ = [("event", C.c_void_p * 10), ("wait_before_bwd", C.c_void_p)]
 
 
 class DiffusError(RuntimeError):

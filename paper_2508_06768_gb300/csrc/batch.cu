@@ -523,6 +523,9 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     mark(DIFFUS_TR_FWD_END);
     if ((rc = launch_status())) return rc;
     if (!bwd) return DIFFUS_OK;
+    if (trace && trace->wait_before_bwd &&
+        cudaStreamWaitEvent(s, (cudaEvent_t)trace->wait_before_bwd, 0) != cudaSuccess)
+        return DIFFUS_E_LAUNCH;
 
     if (((uintptr_t)grad_images) % 4 || (grad_vol && ((uintptr_t)grad_vol) % 4) ||
         (grad_poses && ((uintptr_t)grad_poses) % 4))
