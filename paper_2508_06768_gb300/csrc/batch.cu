@@ -229,15 +229,22 @@ __global__ void k_batch_row_gain(const float *in, float *out, BatchDev B)
     }
 }
 
+// One warp per strip, strips taken from a ticket queue over the plan's
+// widest-first list, so the long strips start first and the warps finish
+// together.
 template <bool TRANSPOSE, int WT>
 __global__ void __launch_bounds__(kBlurWarps * 32) k_batch_blur(const float *__restrict__ in, float *__restrict__ out,
                                                                 const PlanPose *__restrict__ poses,
                                                                 const BlurTile *__restrict__ tiles, int64_t n_tiles,
-                                                                BlurArgs b)
+                                                                BlurArgs b, unsigned *__restrict__ counter)
 {
-    const int64_t nw = (int64_t)gridDim.x * kBlurWarps;
-    for (int64_t t = (int64_t)blockIdx.x * kBlurWarps + (threadIdx.x >> 5); t < n_tiles; t += nw) {
-        const BlurTile tl = tiles[t];
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned q = 0;
+        if (lane == 0) q = atomicAdd(counter, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if ((int64_t)q >= n_tiles) break;
+        const BlurTile tl = tiles[q];
         const PlanPose pp = poses[tl.pose];
         blur_strip<TRANSPOSE, WT>(in + pp.img_off, out + pp.img_off, pp.n_rays, pp.S, b, tl.k0, 0, pp.n_rays);
     }
@@ -245,14 +252,18 @@ __global__ void __launch_bounds__(kBlurWarps * 32) k_batch_blur(const float *__r
 
 template <bool TRANSPOSE>
 void launch_batch_blur(const float *in, float *out, const PlanPose *poses, const BlurTile *tiles, int64_t n_tiles,
-                       const BlurArgs &b, int grid, cudaStream_t s)
+                       const BlurArgs &b, int grid, unsigned *counter, cudaStream_t s)
 {
     switch (b.W) {
-#define DFS_BB(WT)                                                                                        \
-    case WT: k_batch_blur<TRANSPOSE, WT><<<grid, kBlurWarps * 32, 0, s>>>(in, out, poses, tiles, n_tiles, b); break;
+#define DFS_BB(WT)                                                                                               \
+    case WT:                                                                                                     \
+        k_batch_blur<TRANSPOSE, WT><<<grid, kBlurWarps * 32, 0, s>>>(in, out, poses, tiles, n_tiles, b, counter); \
+        break;
     DFS_BB(0) DFS_BB(1) DFS_BB(2) DFS_BB(3) DFS_BB(4) DFS_BB(5) DFS_BB(6) DFS_BB(7) DFS_BB(8)
 #undef DFS_BB
-    default: k_batch_blur<TRANSPOSE, -1><<<grid, kBlurWarps * 32, 0, s>>>(in, out, poses, tiles, n_tiles, b); break;
+    default:
+        k_batch_blur<TRANSPOSE, -1><<<grid, kBlurWarps * 32, 0, s>>>(in, out, poses, tiles, n_tiles, b, counter);
+        break;
     }
 }
 
@@ -519,7 +530,7 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     const int tgrid = (int)std::min<int64_t>((H.n_tiles + kBlurWarps - 1) / kBlurWarps, (int64_t)sm_count() * 16);
     const PlanPose *dpose = at<PlanPose>(plan_dev, H.off_pose);
     const BlurTile *dtiles = at<BlurTile>(plan_dev, H.off_tiles);
-    if (prm->blur) launch_batch_blur<false>(L.y, images, dpose, dtiles, H.n_tiles, bl, tgrid, s);
+    if (prm->blur) launch_batch_blur<false>(L.y, images, dpose, dtiles, H.n_tiles, bl, tgrid, L.counter + 2, s);
     mark(DIFFUS_TR_FWD_END);
     if ((rc = launch_status())) return rc;
     if (!bwd) return DIFFUS_OK;
@@ -532,7 +543,7 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
         return DIFFUS_E_ALIGN;
     const float *gy = grad_images;
     if (prm->blur) {
-        launch_batch_blur<true>(grad_images, L.gy, dpose, dtiles, H.n_tiles, bl, tgrid, s);
+        launch_batch_blur<true>(grad_images, L.gy, dpose, dtiles, H.n_tiles, bl, tgrid, L.counter + 3, s);
         gy = L.gy;
     }
     if (prm->atten) {   // the depth gain is a diagonal row factor: its adjoint is itself
