@@ -247,20 +247,25 @@ __global__ void k_unit_bricks(const uint32_t *__restrict__ ustart, const uint32_
     for (uint32_t i = 0; i < c; i++) unit_brick[u0 + i] = (uint32_t)b;
 }
 
-// One warp per unit (grid-stride over all warps): the warp gathers the
-// unit's runs into its own 9^3 accumulator and writes the unit's partial.
-// Warps are independent, so a CTA has no block barriers.
+// One warp per unit, units handed out by a ticket queue: the warp gathers
+// the unit's runs into its own 9^3 accumulator and writes the unit's
+// partial.  Warps are independent, so a CTA has no block barriers.
 __global__ void __launch_bounds__(kGatherWarps * 32)
     k_gather_units(const float *__restrict__ gz, const Run *__restrict__ runs, const uint32_t *__restrict__ sorted_vals,
                    const uint32_t *__restrict__ bstart, const uint32_t *__restrict__ bend,
                    const uint32_t *__restrict__ ustart, const uint32_t *__restrict__ unit_brick,
-                   const uint32_t *__restrict__ n_units, GatherArgs G, float *__restrict__ upart)
+                   const uint32_t *__restrict__ n_units, GatherArgs G, float *__restrict__ upart,
+                   uint32_t *__restrict__ queue)
 {
     __shared__ GatherSmem sm;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t total = *n_units;
     float *acc = sm.acc[w];
-    for (uint32_t u = blockIdx.x * kGatherWarps + w; u < total; u += gridDim.x * kGatherWarps) {
+    for (;;) {
+        uint32_t u = 0;
+        if (lane == 0) u = atomicAdd(queue, 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= total) break;
         const int b = (int)unit_brick[u];
         const uint32_t part = u - ustart[b];
         const uint32_t r0 = bstart[b] + part * kUnitRuns;
@@ -349,7 +354,7 @@ int runs_per_ray(const diffus_volume_desc *vd, double max_path_mm)
 struct GatherLayout {
     Run *runs;
     uint32_t *keys[2], *vals[2];
-    uint32_t *hist, *sums, *misc;   // misc: [0] units total, [1] scan total
+    uint32_t *hist, *sums, *misc;   // misc: [0] units total, [1] scan total, [2] unit queue
     uint32_t *bstart, *bend, *ucount, *ustart, *unit_brick;
     float *upart;
     size_t bytes;
@@ -431,8 +436,10 @@ int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_r
     launch_scan(L.ucount, L.ustart, (size_t)nb, L.sums, L.misc + 0, s);
     k_unit_bricks<<<(nb + 255) / 256, 256, 0, s>>>(L.ustart, L.ucount, nb, L.unit_brick);
     record_mark(marks.units, marks.external, s);
+    if (cudaMemsetAsync(L.misc + 2, 0, sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
     k_gather_units<<<sms * ctas_per_sm, kGatherWarps * 32, 0, s>>>(gz, L.runs, L.vals[cur], L.bstart, L.bend,
-                                                                  L.ustart, L.unit_brick, L.misc + 0, G, L.upart);
+                                                                  L.ustart, L.unit_brick, L.misc + 0, G, L.upart,
+                                                                  L.misc + 2);
     record_mark(marks.reduce, marks.external, s);
     const size_t nv = (size_t)vd->nx * vd->ny * vd->nz;
     k_voxel_reduce<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(L.upart, L.ustart, L.ucount, G, grad_vol);
