@@ -334,6 +334,77 @@ def run_forms(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, stream,
     out["speedup_fwd_vs_plain"] = out["plain_fwd"]["ms"] / fwd_ms
     del img, gv, wsp
     out.update(run_scale_form(torch, flush, stream, steps, warmup))
+    out.update(run_next_rows(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, stream, steps, warmup, total))
+    return out
+
+
+def _time_fn(torch, fn, flush, stream, steps, warmup):
+    for _ in range(warmup):
+        flush.zero_()
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
+def run_next_rows(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, stream, steps, warmup, total):
+    """Measurements of the rows beyond the hot path: scan conversion (f1),
+    the registration step (f2), the depth-gain attenuation reading (f3) and
+    the CT pre-pass (f4)."""
+    import math
+    from paper_2508_06768_gb300.render import BatchRenderer, ScanConverter, render
+    out = {}
+    dev = vol_d.device
+    # f1: 64 polar images of the 256-ray x 1024-row brain-slice fan onto a 1024 x 1024 grid
+    fan2 = I.Fan(256, 1024, math.radians(70.0), 120.0, 7.0, 0.5)
+    conv = ScanConverter(fan2, 1024, 1024, device=dev)
+    imgs = torch.randn((64, 256, 1024), device=dev)
+    disp = torch.empty((64, 1024, 1024), device=dev)
+    gimg = torch.empty_like(imgs)
+    ms_f = _time_fn(torch, lambda: B.scan_convert(imgs, conv.plan_host, conv.plan_dev, disp), flush, stream,
+                    steps, warmup)
+    ms_b = _time_fn(torch, lambda: B.scan_convert_bwd(disp, conv.plan_host, conv.plan_dev, gimg), flush, stream,
+                    steps, warmup)
+    npix, nq = 64 * 1024 * 1024, 64 * 256 * 1024
+    # forward: one 16-byte tap per pixel (the map is shared by the 64 images:
+    # counted once), 4 B written per pixel, the polar images read once
+    fb = 4.0 * npix + 16.0 * 1024 * 1024 + 4.0 * nq
+    out["f1_scan_convert_fwd"] = {"ms": ms_f, "GB_s": fb / (ms_f * 1e-3) / 1e9,
+                                  "workload": "64 images 256 rays x 1024 rows -> 1024 x 1024, bilinear"}
+    out["f1_scan_convert_bwd"] = {"ms": ms_b, "workload": "adjoint of the same, per polar pixel in a fixed order"}
+    # f2: one registration step (forward + pose gradient) on the 64^3 phantom
+    vs, ps, fs, prs = I.workload_small()
+    prs = prs.with_(mode=1)
+    v1 = torch.from_numpy(vs.data).to(dev)
+    pose = torch.from_numpy(ps).to(dev).requires_grad_(True)
+    tgt = torch.zeros((fs.n_rays, fs.n_samples), device=dev)
+
+    def reg_step():
+        img, _ = render(v1, pose, fs, prs, spacing=vs.spacing, origin=vs.origin)
+        ((img - tgt) ** 2).mean().backward()
+    out["f2_registration_step"] = {"ms": _time_fn(torch, reg_step, flush, stream, steps, warmup),
+                                   "workload": "64^3 phantom, 64 rays x 256 rows: forward + pose gradient"}
+    # f3: the config-4 batch forward+backward with the depth-gain reading
+    ra = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm.with_(atten=1), schedule=sched, with_bwd=True)
+    g = _capture(torch, lambda s: ra.run(poses_d, G, stream=s))
+    ms = _time_graph(torch, g, flush, stream, steps, warmup)
+    out["f3_batched_fwd_bwd_depth_gain"] = {"value": total / (ms * 1e-3), "ms": ms}
+    del g, ra
+    # f4: HU -> impedance over a 256^3 int16 volume to FP32
+    hu = torch.randint(-1000, 3000, (256, 256, 256), dtype=torch.int16, device=dev)
+    zf = torch.empty(hu.shape, dtype=torch.float32, device=dev)
+    tab_h, tab_z = [-1000.0, -100.0, 0.0, 40.0, 1000.0, 3000.0], [0.0004, 1.38, 1.48, 1.62, 6.0, 7.8]
+    ms = _time_fn(torch, lambda: B.hu_to_z(hu, tab_h, tab_z, out=zf), flush, stream, steps, warmup)
+    out["f4_hu_to_z"] = {"ms": ms, "GB_s": hu.numel() * 6.0 / (ms * 1e-3) / 1e9,
+                         "workload": "256^3 int16 HU -> FP32 impedance, 6-breakpoint table"}
     return out
 
 

@@ -246,7 +246,8 @@ __global__ void __launch_bounds__(kBlurWarps * 32) k_batch_blur(const float *__r
         if ((int64_t)q >= n_tiles) break;
         const BlurTile tl = tiles[q];
         const PlanPose pp = poses[tl.pose];
-        blur_strip<TRANSPOSE, WT>(in + pp.img_off, out + pp.img_off, pp.n_rays, pp.S, b, tl.k0, 0, pp.n_rays);
+        blur_strip<TRANSPOSE, WT>(in + pp.img_off, out + pp.img_off, pp.n_rays, pp.S, b, tl.k0, 0, pp.n_rays,
+                                  pp.l2_hi, pp.l2_lo);
     }
 }
 
@@ -524,9 +525,10 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
                                           ck, mb, grid, prm->refine != 0, s);
     if (rc) return rc;
     const int rgrid = (int)std::min<int64_t>((H.total_rays + 7) / 8, (int64_t)sm_count() * 16);
-    if (prm->atten) k_batch_row_gain<<<rgrid, 256, 0, s>>>(march_out, march_out, B);
+    // the depth gain rides on the blur's output; without blur it is a row pass
+    if (prm->atten && !prm->blur) k_batch_row_gain<<<rgrid, 256, 0, s>>>(march_out, march_out, B);
     mark(DIFFUS_TR_BLUR);
-    BlurArgs bl{(float)prm->sigma0, (float)prm->sigma1, H.blurW};
+    BlurArgs bl{(float)prm->sigma0, (float)prm->sigma1, H.blurW, prm->atten};
     const int tgrid = (int)std::min<int64_t>((H.n_tiles + kBlurWarps - 1) / kBlurWarps, (int64_t)sm_count() * 16);
     const PlanPose *dpose = at<PlanPose>(plan_dev, H.off_pose);
     const BlurTile *dtiles = at<BlurTile>(plan_dev, H.off_tiles);
@@ -546,7 +548,7 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
         launch_batch_blur<true>(grad_images, L.gy, dpose, dtiles, H.n_tiles, bl, tgrid, L.counter + 3, s);
         gy = L.gy;
     }
-    if (prm->atten) {   // the depth gain is a diagonal row factor: its adjoint is itself
+    if (prm->atten && !prm->blur) {   // the depth gain is its own adjoint (with blur it rides on the blur)
         k_batch_row_gain<<<rgrid, 256, 0, s>>>(gy, L.gy, B);
         gy = L.gy;
     }

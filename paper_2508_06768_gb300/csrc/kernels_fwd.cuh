@@ -118,6 +118,7 @@ constexpr int kBlurWarps = 4;    // strips (warps) per CTA
 struct BlurArgs {
     float sigma0, sigma1;
     int W;
+    int gain;              // depth-gain reading: the output row k carries a^(2(k+1))
 };
 
 // Gaussian weight of lateral offset m at echo row k (sigma in rays).
@@ -144,11 +145,14 @@ __device__ __forceinline__ float blur_w(const BlurArgs &b, int m, int k, float i
 // reads the window through the cache instead.
 template <bool TRANSPOSE, int WT>
 __device__ void blur_strip(const float *__restrict__ in, float *__restrict__ out, int n, int S,
-                           const BlurArgs &b, int k0, int j0, int j1)
+                           const BlurArgs &b, int k0, int j0, int j1, float l2_hi, float l2_lo)
 {
     const int lane = threadIdx.x & 31;
     const int k = k0 + lane;
     const bool kin = k < S;
+    // the depth gain is constant along the strip lane's row and commutes
+    // with the lateral blur (and its transpose): applied to the output
+    const float gk = (b.gain && kin) ? depth_gain(l2_hi, l2_lo, k) : 1.0f;
     const float invS = 1.0f / (float)S;
     const float *src = in + (kin ? k : 0);
     float *dst = out + (kin ? k : 0);
@@ -194,7 +198,7 @@ __device__ void blur_strip(const float *__restrict__ in, float *__restrict__ out
                 for (int m = 1; m <= WW; m++) acc = fmaf(w[m], win[i + WW - m] + win[i + WW + m], acc);
                 if (kin && j < j1) {
                     if (!TRANSPOSE) acc *= rnorm(j);
-                    dst[(size_t)j * S] = acc;
+                    dst[(size_t)j * S] = acc * gk;
                 }
             }
 #pragma unroll
@@ -221,7 +225,7 @@ __device__ void blur_strip(const float *__restrict__ in, float *__restrict__ out
         float acc = wt(0) * ld(j);
         for (int m = 1; m <= W; m++) acc = fmaf(wt(m), ld(j - m) + ld(j + m), acc);
         if (!TRANSPOSE) acc *= 1.0f / N_of(j);
-        dst[(size_t)j * S] = acc;
+        dst[(size_t)j * S] = acc * gk;
     }
 }
 
@@ -231,12 +235,12 @@ constexpr int kBlurSegRays = 64;
 
 template <bool TRANSPOSE, int WT>
 __global__ void __launch_bounds__(kBlurWarps * 32) k_blur(const float *__restrict__ in, float *__restrict__ out,
-                                                          int n, int S, BlurArgs b)
+                                                          int n, int S, BlurArgs b, float l2_hi, float l2_lo)
 {
     const int strip = blockIdx.x * kBlurWarps + (threadIdx.x >> 5);
     if (strip * kBlurRows >= S) return;
     const int j0 = blockIdx.y * kBlurSegRays;
-    blur_strip<TRANSPOSE, WT>(in, out, n, S, b, strip * kBlurRows, j0, min(n, j0 + kBlurSegRays));
+    blur_strip<TRANSPOSE, WT>(in, out, n, S, b, strip * kBlurRows, j0, min(n, j0 + kBlurSegRays), l2_hi, l2_lo);
 }
 
 }  // namespace dfs

@@ -7,7 +7,8 @@ using namespace dfs;
 
 namespace dfs {
 
-int launch_blur(const float *in, float *out, int n, int S, const diffus_params *prm, bool transpose, cudaStream_t s);
+int launch_blur(const float *in, float *out, int n, int S, const diffus_params *prm, const diffus_fan *fan,
+                bool transpose, cudaStream_t s);
 int check_common(const void *vol, const diffus_volume_desc *vd, const float *pose, const diffus_fan *fan,
                  const diffus_params *prm);
 
@@ -128,10 +129,10 @@ extern "C" int diffus_render_bwd(const void *vol, const diffus_volume_desc *vd, 
     k_offsets<<<(n + 127) / 128, 128, 0, s>>>(L.row_off, L.gz_off, L.ck_off, L.ray0, n, S);
     const float *gy = grad_image;
     if (prm->blur) {
-        if ((rc = launch_blur(grad_image, L.gy, n, S, prm, true, s))) return rc;
+        if ((rc = launch_blur(grad_image, L.gy, n, S, prm, fan, true, s))) return rc;
         gy = L.gy;
     }
-    if (prm->atten) {   // the depth gain is a diagonal row factor: its adjoint is itself
+    if (prm->atten && !prm->blur) {   // the depth gain is its own adjoint (with blur it rides on the blur)
         float hi, lo;
         gain_l2(attenuation_a(fan), hi, lo);
         const int64_t ne = (int64_t)n * S;

@@ -80,17 +80,19 @@ int launch_fwd_march(const void *vol, const diffus_volume_desc *vd, const float 
     return launch_status();
 }
 
-int launch_blur(const float *in, float *out, int n, int S, const diffus_params *prm, bool transpose,
-                cudaStream_t s)
+int launch_blur(const float *in, float *out, int n, int S, const diffus_params *prm, const diffus_fan *fan,
+                bool transpose, cudaStream_t s)
 {
-    BlurArgs b{(float)prm->sigma0, (float)prm->sigma1, blur_halfwidth(prm)};
+    BlurArgs b{(float)prm->sigma0, (float)prm->sigma1, blur_halfwidth(prm), prm->atten};
+    float hi = 0.0f, lo = 0.0f;
+    if (prm->atten) gain_l2(attenuation_a(fan), hi, lo);
     const int strips = (S + kBlurRows - 1) / kBlurRows;
     const dim3 grid((strips + kBlurWarps - 1) / kBlurWarps, (n + kBlurSegRays - 1) / kBlurSegRays);
 #define DFS_BLUR(WT)                                                        \
     if (transpose)                                                          \
-        k_blur<true, WT><<<grid, kBlurWarps * 32, 0, s>>>(in, out, n, S, b); \
+        k_blur<true, WT><<<grid, kBlurWarps * 32, 0, s>>>(in, out, n, S, b, hi, lo); \
     else                                                                    \
-        k_blur<false, WT><<<grid, kBlurWarps * 32, 0, s>>>(in, out, n, S, b);
+        k_blur<false, WT><<<grid, kBlurWarps * 32, 0, s>>>(in, out, n, S, b, hi, lo);
     switch (b.W) {
     case 0: DFS_BLUR(0) break;
     case 1: DFS_BLUR(1) break;
@@ -126,13 +128,13 @@ extern "C" int diffus_render_fwd(const void *vol, const diffus_volume_desc *vd, 
     if (status && cudaMemsetAsync(status, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
     float *march_out = prm->blur ? L.y : image;
     if ((rc = launch_fwd_march(vol, vd, pose, fan, prm, L.geo, march_out, ray_valid, status, s))) return rc;
-    if (prm->atten) {
+    if (prm->atten && !prm->blur) {   // with blur the gain rides on the blur's output
         float hi, lo;
         gain_l2(attenuation_a(fan), hi, lo);
         const int64_t ne = (int64_t)fan->n_rays * fan->n_samples;
         k_row_gain<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(march_out, march_out, fan->n_rays, fan->n_samples, hi,
                                                                 lo);
     }
-    if (prm->blur) rc = launch_blur(L.y, image, fan->n_rays, fan->n_samples, prm, false, s);
+    if (prm->blur) rc = launch_blur(L.y, image, fan->n_rays, fan->n_samples, prm, fan, false, s);
     return rc;
 }

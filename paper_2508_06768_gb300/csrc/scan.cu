@@ -7,7 +7,8 @@
 // map as a CSR list per polar pixel (display pixel, weight) in pixel order.
 // The forward kernel gathers 4 polar values per display pixel; the adjoint
 // kernel gathers, per polar pixel, the weighted display gradients of its
-// list, so it needs no atomics and its sums have a fixed order.
+// list, so it needs no atomics and its sums have a fixed order.  Both read
+// their tap or list once for all images of a call.
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -110,35 +111,49 @@ ScanHeader scan_layout(const ScanGeom &g, int64_t n_ent)
     return h;
 }
 
+// One thread per display pixel: the tap is read once and applied to all
+// `count` images.
 __global__ void k_scan_fwd(const float *__restrict__ img, const ScanTap *__restrict__ map, int S, int64_t img_stride,
-                           int64_t npix, float *__restrict__ out)
+                           int64_t npix, int count, float *__restrict__ out)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
-    const float *im = img + (int64_t)blockIdx.y * img_stride;
     const ScanTap t = map[p];
-    float v = 0.0f;
-    if (t.j0 >= 0) {
-        const float *r0 = im + (int64_t)t.j0 * S + t.k0, *r1 = r0 + S;
-        const float a = (1.0f - t.fv) * (1.0f - t.fu), b = t.fv * (1.0f - t.fu);
-        const float c = (1.0f - t.fv) * t.fu, d = t.fv * t.fu;
-        v = fmaf(d, __ldg(r1 + 1), fmaf(c, __ldg(r0 + 1), fmaf(b, __ldg(r1), a * __ldg(r0))));
+    if (t.j0 < 0) {
+        for (int c = 0; c < count; c++) out[(int64_t)c * npix + p] = 0.0f;
+        return;
     }
-    out[(int64_t)blockIdx.y * npix + p] = v;
+    const float a = (1.0f - t.fv) * (1.0f - t.fu), b = t.fv * (1.0f - t.fu);
+    const float cc = (1.0f - t.fv) * t.fu, d = t.fv * t.fu;
+    const int64_t o = (int64_t)t.j0 * S + t.k0;
+    for (int c = 0; c < count; c++) {
+        const float *r0 = img + (int64_t)c * img_stride + o, *r1 = r0 + S;
+        out[(int64_t)c * npix + p] = fmaf(d, __ldg(r1 + 1), fmaf(cc, __ldg(r0 + 1), fmaf(b, __ldg(r1), a * __ldg(r0))));
+    }
 }
 
+// One thread per polar pixel: its list is read once and applied to all
+// `count` gradients, each summed in the list's fixed order.
 __global__ void k_scan_bwd(const float *__restrict__ gout, const uint32_t *__restrict__ rowptr,
-                           const ScanEnt *__restrict__ ent, int64_t nq, int64_t npix, float *__restrict__ gimg)
+                           const ScanEnt *__restrict__ ent, int64_t nq, int64_t npix, int count,
+                           float *__restrict__ gimg)
 {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
-    const float *go = gout + (int64_t)blockIdx.y * npix;
-    float s = 0.0f;
-    for (uint32_t e = rowptr[q], e1 = rowptr[q + 1]; e < e1; e++) {
-        const ScanEnt en = ent[e];
-        s = fmaf(en.w, __ldg(go + en.pixel), s);
+    const uint32_t e0 = rowptr[q], e1 = rowptr[q + 1];
+    for (int c0 = 0; c0 < count; c0 += 4) {
+        // four images per pass over the list
+        float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (uint32_t e = e0; e < e1; e++) {
+            const ScanEnt en = ent[e];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (c0 + u < count) s4[u] = fmaf(en.w, __ldg(gout + (int64_t)(c0 + u) * npix + en.pixel), s4[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (c0 + u < count) gimg[(int64_t)(c0 + u) * nq + q] = s4[u];
     }
-    gimg[(int64_t)blockIdx.y * nq + q] = s;
 }
 
 int check_scan_plan(const void *plan_host, const void *plan_dev)
@@ -223,9 +238,8 @@ extern "C" int diffus_scan_convert(const float *images, int32_t count, const voi
     if (((uintptr_t)images) % 4 || ((uintptr_t)out) % 4) return DIFFUS_E_ALIGN;
     const ScanHeader &h = *(const ScanHeader *)plan_host;
     const int64_t npix = (int64_t)h.W * h.H;
-    const dim3 grid((unsigned)((npix + 255) / 256), (unsigned)count);
-    k_scan_fwd<<<grid, 256, 0, (cudaStream_t)stream>>>(images, at<ScanTap>(plan_dev, h.off_map), h.S,
-                                                       (int64_t)h.n * h.S, npix, out);
+    k_scan_fwd<<<(unsigned)((npix + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        images, at<ScanTap>(plan_dev, h.off_map), h.S, (int64_t)h.n * h.S, npix, count, out);
     return launch_status();
 }
 
@@ -239,9 +253,8 @@ extern "C" int diffus_scan_convert_bwd(const float *grad_out, int32_t count, con
     if (((uintptr_t)grad_out) % 4 || ((uintptr_t)grad_images) % 4) return DIFFUS_E_ALIGN;
     const ScanHeader &h = *(const ScanHeader *)plan_host;
     const int64_t nq = (int64_t)h.n * h.S;
-    const dim3 grid((unsigned)((nq + 255) / 256), (unsigned)count);
-    k_scan_bwd<<<grid, 256, 0, (cudaStream_t)stream>>>(grad_out, at<uint32_t>(plan_dev, h.off_rowptr),
-                                                       at<ScanEnt>(plan_dev, h.off_ent), nq,
-                                                       (int64_t)h.W * h.H, grad_images);
+    k_scan_bwd<<<(unsigned)((nq + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        grad_out, at<uint32_t>(plan_dev, h.off_rowptr), at<ScanEnt>(plan_dev, h.off_ent), nq, (int64_t)h.W * h.H,
+        count, grad_images);
     return launch_status();
 }

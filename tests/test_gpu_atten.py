@@ -12,10 +12,11 @@ from tests.helpers import (COND_DET_GRAD, FP32_TOL, GRAD_TOL, NEAR_POLE_TOL, che
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_depth_gain_forward_and_gradients(mode):
+@pytest.mark.parametrize("mode,blur", [(0, 1), (1, 1), (1, 0)])
+def test_depth_gain_forward_and_gradients(mode, blur):
+    # with blur the gain is applied by the blur kernels, without by a row pass
     vol, pose, fan, prm = I.workload_small()
-    prm = prm.with_(mode=mode, atten=1)
+    prm = prm.with_(mode=mode, atten=1, blur=blur)
     img, valid, status = gpu_render(vol, pose, fan, prm)
     ref, first, det = oracle_render(vol, pose, fan, prm)
     S, W = fan.n_samples, oracle.blur_halfwidth(prm)
