@@ -363,6 +363,7 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
                                  const diffus_params *prm, const diffus_schedule *sched, void *plan_host,
                                  size_t plan_bytes, int64_t *img_offsets, size_t *ws_fwd, size_t *ws_bwd)
 {
+    NvtxRange nvtx_range("diffus_batch_plan");
     int rc;
     if ((rc = check_vol(vd))) return rc;
     if ((rc = check_params(prm))) return rc;
@@ -470,6 +471,7 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
                                    float *grad_poses, uint32_t *status, void *workspace, size_t ws_bytes,
                                    const diffus_trace *trace, diffus_stream_t stream)
 {
+    NvtxRange nvtx_range("diffus_render_batch");
     int rc;
     if ((rc = check_vol(vd))) return rc;
     if ((rc = check_params(prm))) return rc;

@@ -1,6 +1,8 @@
 // Host-side validation and workspace layout shared by the entry points.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -74,6 +76,15 @@ inline void gain_l2(double a, float &hi, float &lo)
     hi = (float)l2;
     lo = (float)(l2 - (double)hi);
 }
+
+// NVTX range around one C-ABI call (header-only NVTX3: near free when no
+// profiler is attached), so profiler timelines show the library's calls.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 inline double attenuation_a(const diffus_fan *f)
 {

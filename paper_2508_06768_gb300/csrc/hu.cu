@@ -77,6 +77,7 @@ __global__ void k_hu_to_z(const int16_t *__restrict__ hu, int64_t n, HuTable tab
 extern "C" int diffus_hu_to_z(const int16_t *hu, int64_t n, const double *hu_pts, const double *z_pts, int32_t m,
                               void *z_out, int32_t out_dtype, diffus_stream_t stream)
 {
+    NvtxRange nvtx_range("diffus_hu_to_z");
     if (!hu || !hu_pts || !z_pts || !z_out) return DIFFUS_E_NULL;
     if (n < 0 || m < 1 || m > kHuMax) return DIFFUS_E_PARAM;
     if (out_dtype != DIFFUS_F32 && out_dtype != DIFFUS_BF16) return DIFFUS_E_DTYPE;

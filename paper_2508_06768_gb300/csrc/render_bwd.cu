@@ -112,6 +112,7 @@ extern "C" int diffus_render_bwd(const void *vol, const diffus_volume_desc *vd, 
                                  float *grad_vol, float *grad_pose, uint32_t *status, void *workspace,
                                  size_t ws_bytes, diffus_stream_t stream)
 {
+    NvtxRange nvtx_range("diffus_render_bwd");
     int rc = check_common(vol, vd, pose, fan, prm);
     if (rc) return rc;
     if (!grad_image) return DIFFUS_E_NULL;

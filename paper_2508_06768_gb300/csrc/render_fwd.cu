@@ -116,6 +116,7 @@ extern "C" int diffus_render_fwd(const void *vol, const diffus_volume_desc *vd, 
                                  int32_t *ray_valid, uint32_t *status, void *workspace, size_t ws_bytes,
                                  diffus_stream_t stream)
 {
+    NvtxRange nvtx_range("diffus_render_fwd");
     int rc = check_common(vol, vd, pose, fan, prm);
     if (rc) return rc;
     if (!image) return DIFFUS_E_NULL;

@@ -177,6 +177,7 @@ extern "C" size_t diffus_scan_plan_bytes(const diffus_fan *fan, const diffus_sca
 extern "C" int diffus_scan_plan(const diffus_fan *fan, const diffus_scan_grid *grid, void *plan_host,
                                 size_t plan_bytes)
 {
+    NvtxRange nvtx_range("diffus_scan_plan");
     ScanGeom g;
     int rc = scan_geom(fan, grid, g);
     if (rc) return rc;
@@ -231,6 +232,7 @@ extern "C" int diffus_scan_plan(const diffus_fan *fan, const diffus_scan_grid *g
 extern "C" int diffus_scan_convert(const float *images, int32_t count, const void *plan_host, const void *plan_dev,
                                    float *out, diffus_stream_t stream)
 {
+    NvtxRange nvtx_range("diffus_scan_convert");
     int rc = check_scan_plan(plan_host, plan_dev);
     if (rc) return rc;
     if (!images || !out) return DIFFUS_E_NULL;
@@ -246,6 +248,7 @@ extern "C" int diffus_scan_convert(const float *images, int32_t count, const voi
 extern "C" int diffus_scan_convert_bwd(const float *grad_out, int32_t count, const void *plan_host,
                                        const void *plan_dev, float *grad_images, diffus_stream_t stream)
 {
+    NvtxRange nvtx_range("diffus_scan_convert_bwd");
     int rc = check_scan_plan(plan_host, plan_dev);
     if (rc) return rc;
     if (!grad_out || !grad_images) return DIFFUS_E_NULL;
