@@ -122,7 +122,7 @@ def build_workload(rank=0, count=512, n=256):
 # Kernels of one batched step, with the phase events that bracket them:
 # name -> (first event, last event) of diffus_render_batch's trace.
 TRACE = {"ray_setup": (0, 1), "march_fwd": (1, 2), "blur": (2, 3), "blur_T": (3, 4), "march_bwd": (4, 5),
-         "pose_reduce": (5, 6), "gather_sort": (6, 8), "gather_units": (8, 9), "voxel_reduce": (9, 7)}
+         "gather_sort": (5, 8), "gather_units": (8, 9), "voxel_reduce": (9, 6), "pose_reduce": (6, 7)}
 N_EVENTS = 10
 
 # Algorithmic work per ray-sample of each kernel (derivation in the design

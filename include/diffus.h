@@ -210,9 +210,9 @@ enum {
     DIFFUS_TR_BLUR = 2,        /* after the forward march */
     DIFFUS_TR_FWD_END = 3,     /* after the lateral blur */
     DIFFUS_TR_MARCH_BWD = 4,   /* after the blur transpose */
-    DIFFUS_TR_POSE = 5,        /* after the adjoint march */
-    DIFFUS_TR_GATHER = 6,      /* after the pose reduction */
-    DIFFUS_TR_END = 7,         /* after the volume gather */
+    DIFFUS_TR_GATHER = 5,      /* after the adjoint march, before the volume gather */
+    DIFFUS_TR_POSE = 6,        /* after the volume gather, before the pose reduction */
+    DIFFUS_TR_END = 7,         /* after the pose reduction */
     DIFFUS_TR_GATHER_UNITS = 8,  /* inside the gather: before the brick-unit kernel */
     DIFFUS_TR_GATHER_REDUCE = 9, /* inside the gather: before the per-voxel reduction */
     DIFFUS_TR_COUNT = 10

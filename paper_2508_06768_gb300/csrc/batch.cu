@@ -188,15 +188,15 @@ __global__ void __launch_bounds__(WARPS * 32, REFINE ? 1 : kFwdThreadsPerSM / (W
     }
 }
 
-template <typename T, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, kBwdThreadsPerSM / (WARPS * 32)) k_batch_bwd(const T *__restrict__ vol, MarchArgs A, BatchDev B,
+template <typename T, int WARPS, bool POSE>
+__global__ void __launch_bounds__(WARPS * 32, (POSE ? kBwdThreadsPerSM : kBwdValThreadsPerSM) / (WARPS * 32)) k_batch_bwd(const T *__restrict__ vol, MarchArgs A, BatchDev B,
                                                           const RayGeo *__restrict__ geo,
                                                           const float *__restrict__ gy, float *__restrict__ gz,
                                                           double *__restrict__ part, float4 *__restrict__ ckpt,
                                                           unsigned *__restrict__ counter,
                                                           const float *__restrict__ mbuf)
 {
-    __shared__ BwdSmem sm[WARPS];
+    __shared__ BwdSmem<POSE> sm[WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
         unsigned q = 0;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(WARPS * 32, kBwdThreadsPerSM / (WARPS * 32)) k
             Ap.a2 = B.pose[rg.pose].a2;
             Ap.a2d = B.pose[rg.pose].a2d;
         }
-        march_bwd_ray<T>(vol, Ap, rg, gy + B.row_off[r], gz + B.gz_off[r], part + 6 * (size_t)r,
+        march_bwd_ray<T, POSE>(vol, Ap, rg, gy + B.row_off[r], gz + B.gz_off[r], part + 6 * (size_t)r,
                          ckpt + B.ck_off[r], sm[w], true, mbuf ? mbuf + B.row_off[r] : nullptr);
         __syncwarp();
     }
@@ -291,10 +291,15 @@ void launch_fwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const 
 
 template <typename T, int WARPS>
 void launch_bwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, const float *gy,
-                  float *gz, double *part, float4 *ckpt, unsigned *counter, const float *mbuf, int grid,
+                  float *gz, double *part, float4 *ckpt, unsigned *counter, const float *mbuf, int grid, bool pose,
                   cudaStream_t s)
 {
-    k_batch_bwd<T, WARPS><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf);
+    if (pose)
+        k_batch_bwd<T, WARPS, true><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, gy, gz, part, ckpt,
+                                                                counter, mbuf);
+    else
+        k_batch_bwd<T, WARPS, false><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, gy, gz, part, ckpt,
+                                                                 counter, mbuf);
 }
 
 template <typename T>
@@ -313,12 +318,13 @@ int launch_fwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev 
 
 template <typename T>
 int launch_bwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, const float *gy,
-                 float *gz, double *part, float4 *ckpt, unsigned *counter, const float *mbuf, int grid, cudaStream_t s)
+                 float *gz, double *part, float4 *ckpt, unsigned *counter, const float *mbuf, int grid, bool pose,
+                 cudaStream_t s)
 {
     switch (warps) {
-    case 2: launch_bwd_t<T, 2>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, grid, s); break;
-    case 4: launch_bwd_t<T, 4>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, grid, s); break;
-    case 8: launch_bwd_t<T, 8>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, grid, s); break;
+    case 2: launch_bwd_t<T, 2>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, grid, pose, s); break;
+    case 4: launch_bwd_t<T, 4>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, grid, pose, s); break;
+    case 8: launch_bwd_t<T, 8>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, grid, pose, s); break;
     default: return DIFFUS_E_PLAN;
     }
     return DIFFUS_OK;
@@ -555,15 +561,16 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
         gy = L.gy;
     }
     mark(DIFFUS_TR_MARCH_BWD);
+    // with a volume gradient the gather also forms the pose terms, so the
+    // adjoint march samples values only
+    const bool march_pose = grad_poses && !grad_vol;
     if (vd->dtype == DIFFUS_F32)
-        rc = launch_bwd_w<float>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, L.mbuf, grid, s);
+        rc = launch_bwd_w<float>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, L.mbuf, grid,
+                                 march_pose, s);
     else
         rc = launch_bwd_w<unsigned short>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, L.mbuf,
-                                          grid, s);
+                                          grid, march_pose, s);
     if (rc) return rc;
-    mark(DIFFUS_TR_POSE);
-    const int32_t *ray0 = at<int32_t>(plan_dev, H.off_ray0);
-    if (grad_poses) k_pose_reduce_batch<<<(H.P + 3) / 4, 128, 0, s>>>(L.part, ray0, H.P, grad_poses);
     mark(DIFFUS_TR_GATHER);
     if (grad_vol) {
         GatherMarks gm;
@@ -572,9 +579,13 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
             gm.reduce = (cudaEvent_t)trace->event[DIFFUS_TR_GATHER_REDUCE];
             gm.external = external;
         }
-        rc = launch_gather(vd, L.geo, H.total_rays, H.max_depth, L.gz, (const long long *)B.gz_off, L.gather_ws,
-                           status, grad_vol, H.gather_ctas, s, gm);
+        rc = launch_gather(vd, vol, L.geo, H.total_rays, H.max_depth, L.gz, (const long long *)B.gz_off, L.gather_ws,
+                           status, grad_vol, grad_poses ? L.part : nullptr, H.gather_ctas, s, gm);
+        if (rc) return rc;
     }
+    mark(DIFFUS_TR_POSE);
+    const int32_t *ray0 = at<int32_t>(plan_dev, H.off_ray0);
+    if (grad_poses) k_pose_reduce_batch<<<(H.P + 3) / 4, 128, 0, s>>>(L.part, ray0, H.P, grad_poses);
     mark(DIFFUS_TR_END);
-    return rc ? rc : launch_status();
+    return launch_status();
 }

@@ -17,8 +17,11 @@ constexpr int kChunk = 8;                    // interfaces per lane per segment
 constexpr int kSeg = kWarp * kChunk;         // interfaces per warp segment
 constexpr int kSegPad = kSeg + kSeg / kChunk;  // padded smem row (conflict-free chunk reads)
 // Resident-thread targets of the batched march kernels per SM (launch-bound
-// hints): the adjoint at <= 128 registers, the unrefined forward at <= 85.
+// hints): the adjoint that samples dZ/dp for the pose terms at <= 128
+// registers, the adjoint that samples values only and the unrefined forward
+// at <= 85.
 constexpr int kBwdThreadsPerSM = 512;
+constexpr int kBwdValThreadsPerSM = 768;
 constexpr int kFwdThreadsPerSM = 768;
 constexpr float kPoleEps = 1e-6f;            // det(A_k) threshold of a well-posed depth
 constexpr int kMaxW = 32;                    // largest lateral blur half-width

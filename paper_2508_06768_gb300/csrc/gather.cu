@@ -17,7 +17,7 @@ constexpr int kScanChunk = 4096;
 __global__ void k_ray_runs(const RayGeo *__restrict__ geo, const long long *__restrict__ gz_off, int n_rays,
                            GatherArgs G, int cap, uint32_t sentinel,
                            Run *__restrict__ runs, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                           uint32_t *__restrict__ status)
+                           int *__restrict__ nrun, uint32_t *__restrict__ status)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rays) return;
@@ -49,7 +49,7 @@ __global__ void k_ray_runs(const RayGeo *__restrict__ geo, const long long *__re
             run.dZ = rg.DX[2];
             run.g_off = gz_off[r] + k;
             run.len = (int)(k1 - k + 1);
-            run.pad = 0;
+            run.k0 = (int)k;
             const size_t slot = (size_t)cnt * n_rays + r;
             runs[slot] = run;
             keys[slot] = brick;
@@ -74,6 +74,7 @@ __global__ void k_ray_runs(const RayGeo *__restrict__ geo, const long long *__re
         keys[slot] = sentinel;
         vals[slot] = (uint32_t)slot;
     }
+    nrun[r] = cnt;
 }
 
 // ------------------------------------------------------------ exclusive scan
@@ -249,15 +250,17 @@ __global__ void k_unit_bricks(const uint32_t *__restrict__ ustart, const uint32_
 
 // One warp per unit, units handed out by a ticket queue: the warp gathers
 // the unit's runs into its own 9^3 accumulator and writes the unit's
-// partial.  Warps are independent, so a CTA has no block barriers.
+// partial (with POSE, also each run's pose-gradient sums).  Warps are
+// independent, so a CTA has no block barriers.
+template <typename T, bool POSE>
 __global__ void __launch_bounds__(kGatherWarps * 32)
     k_gather_units(const float *__restrict__ gz, const Run *__restrict__ runs, const uint32_t *__restrict__ sorted_vals,
                    const uint32_t *__restrict__ bstart, const uint32_t *__restrict__ bend,
                    const uint32_t *__restrict__ ustart, const uint32_t *__restrict__ unit_brick,
                    const uint32_t *__restrict__ n_units, GatherArgs G, float *__restrict__ upart,
-                   uint32_t *__restrict__ queue)
+                   uint32_t *__restrict__ queue, const T *__restrict__ vol, PoseOut po)
 {
-    __shared__ GatherSmem sm;
+    __shared__ GatherSmem<POSE> sm;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t total = *n_units;
     float *acc = sm.acc[w];
@@ -273,8 +276,20 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
         r1 = r1 < bend[b] ? r1 : bend[b];
         const int bx0 = (b % G.nbx) * kBrick, by0 = ((b / G.nbx) % G.nby) * kBrick, bz0 = (b / (G.nbx * G.nby)) * kBrick;
         for (int i = lane; i < kBrickVox; i += 32) acc[i] = 0.0f;
+        if (POSE) {
+            // the 9^3 voxels the brick's cells touch (clamped at the far faces,
+            // where no cell of the brick reaches)
+            const unsigned sy = (unsigned)G.nx, sz = (unsigned)G.nx * (unsigned)G.ny;
+#pragma unroll 8
+            for (int i = lane; i < kBrickVox; i += 32) {   // eight loads in flight per lane
+                const int lx = i % kBrickV, ly = (i / kBrickV) % kBrickV, lz = i / (kBrickV * kBrickV);
+                const unsigned x = (unsigned)min(bx0 + lx, G.nx - 1), y = (unsigned)min(by0 + ly, G.ny - 1),
+                               z = (unsigned)min(bz0 + lz, G.nz - 1);
+                sm.vox[w][i] = ldv(vol, z * sz + y * sy + x);
+            }
+        }
         __syncwarp();
-        gather_runs(runs, sorted_vals, r0, r1, gz, G, bx0, by0, bz0, sm, w);
+        gather_runs<POSE>(runs, sorted_vals, r0, r1, gz, G, bx0, by0, bz0, sm, w, po);
         __syncwarp();
         float *out = upart + (size_t)u * kBrickVox;
         for (int i = lane; i < kBrickVox; i += 32) out[i] = acc[i];
@@ -317,6 +332,62 @@ __global__ void k_voxel_reduce(const float *__restrict__ upart, const uint32_t *
     grad_vol[v] = s;
 }
 
+// Pose-gradient terms of each ray from its runs' sums, added in slot order
+// (run order along the ray) in FP64: the translation part sum_k dL/dZ_k
+// grad Z(p_k) (per mm) and the rotation part sum_k dL/dZ_k s_k grad Z(p_k)
+// projected on the ray's direction derivatives, s_k = (k + 1/2) ds.
+__global__ void k_ray_pose(const float *__restrict__ rpart, size_t slots, const int *__restrict__ nrun,
+                           const RayGeo *__restrict__ geo, int n_rays, float isx, float isy, float isz,
+                           double *__restrict__ pose_part)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    // compensated FP32 sums (Knuth's two-sum; FP64 arithmetic is slow on
+    // this part), four runs' loads in flight, additions in run order
+    float sum[6] = {0, 0, 0, 0, 0, 0}, err[6] = {0, 0, 0, 0, 0, 0};
+    const int cnt = nrun[r];
+    constexpr int kB = 4;
+    for (int i0 = 0; i0 < cnt; i0 += kB) {
+        float x[kB][6];
+#pragma unroll
+        for (int b = 0; b < kB; b++) {
+            const size_t slot = (size_t)(i0 + b) * n_rays + r;
+#pragma unroll
+            for (int q = 0; q < 6; q++) x[b][q] = i0 + b < cnt ? rpart[(size_t)q * slots + slot] : 0.0f;
+        }
+#pragma unroll
+        for (int b = 0; b < kB; b++) {
+#pragma unroll
+            for (int q = 0; q < 6; q++) {
+                const float t = __fadd_rn(sum[q], x[b][q]);
+                const float z = __fsub_rn(t, sum[q]);
+                const float e = __fadd_rn(__fsub_rn(sum[q], __fsub_rn(t, z)), __fsub_rn(x[b][q], z));
+                err[q] = __fadd_rn(err[q], e);
+                sum[q] = t;
+            }
+        }
+    }
+    double t[3], u[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        t[a] = (double)sum[a] + (double)err[a];
+        u[a] = (double)sum[3 + a] + (double)err[3 + a];
+    }
+    const RayGeo &rg = geo[r];
+    const double is[3] = {(double)isx, (double)isy, (double)isz};
+    const double ds = (double)rg.ds;
+    double *out = pose_part + 6 * (size_t)r;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        t[a] *= is[a];
+        u[a] *= is[a] * ds;
+        out[a] = t[a];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; q++)
+        out[3 + q] = u[0] * (double)rg.v[q][0] + u[1] * (double)rg.v[q][1] + u[2] * (double)rg.v[q][2];
+}
+
 int sort_bits(int nb)
 {
     int bits = 1;
@@ -357,6 +428,8 @@ struct GatherLayout {
     uint32_t *hist, *sums, *misc;   // misc: [0] units total, [1] scan total, [2] unit queue
     uint32_t *bstart, *bend, *ucount, *ustart, *unit_brick;
     float *upart;
+    float *rpart;   // per-run pose-gradient sums, 6 x slots
+    int *nrun;      // runs of each ray
     size_t bytes;
 };
 
@@ -385,6 +458,8 @@ static GatherLayout gather_layout(void *ws, const diffus_volume_desc *vd, long l
     L.ustart = c.take<uint32_t>(nb);
     L.unit_brick = c.take<uint32_t>(max_units);
     L.upart = c.take<float>(max_units * kBrickVox);
+    L.rpart = c.take<float>(6 * slots);
+    L.nrun = c.take<int>((size_t)n_rays);
     L.bytes = c.used;
     return L;
 }
@@ -402,9 +477,18 @@ static void launch_scan(const uint32_t *in, uint32_t *out, size_t n, uint32_t *s
     k_chunk_scan<<<nch, 1024, 0, s>>>(in, n, sums, out);
 }
 
-int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_rays, double max_path_mm,
-                  const float *gz, const long long *gz_off, void *ws, uint32_t *status, float *grad_vol,
-                  int ctas_per_sm, cudaStream_t s, const GatherMarks &marks)
+template <typename T, bool POSE>
+static void launch_units(const float *gz, const GatherLayout &L, int cur, const GatherArgs &G, const void *vol,
+                         const PoseOut &po, int grid, cudaStream_t s)
+{
+    k_gather_units<T, POSE><<<grid, kGatherWarps * 32, 0, s>>>(gz, L.runs, L.vals[cur], L.bstart, L.bend, L.ustart,
+                                                             L.unit_brick, L.misc + 0, G, L.upart, L.misc + 2,
+                                                             (const T *)vol, po);
+}
+
+int launch_gather(const diffus_volume_desc *vd, const void *vol, const RayGeo *geo, long long n_rays,
+                  double max_path_mm, const float *gz, const long long *gz_off, void *ws, uint32_t *status,
+                  float *grad_vol, double *pose_part, int ctas_per_sm, cudaStream_t s, const GatherMarks &marks)
 {
     const GatherArgs G = make_gather_args(vd);
     const int nb = G.nbx * G.nby * G.nbz;
@@ -417,8 +501,8 @@ int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_r
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 
-    k_ray_runs<<<(unsigned)((n_rays + 127) / 128), 128, 0, s>>>(geo, gz_off, (int)n_rays, G, cap, sentinel, L.runs, L.keys[0],
-                                                               L.vals[0], status);
+    k_ray_runs<<<(unsigned)((n_rays + 127) / 128), 128, 0, s>>>(geo, gz_off, (int)n_rays, G, cap, sentinel, L.runs,
+                                                               L.keys[0], L.vals[0], L.nrun, status);
     // stable LSD radix sort by brick
     const int nblk = (int)((slots + kSortTile - 1) / kSortTile);
     int cur = 0;
@@ -437,12 +521,21 @@ int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_r
     k_unit_bricks<<<(nb + 255) / 256, 256, 0, s>>>(L.ustart, L.ucount, nb, L.unit_brick);
     record_mark(marks.units, marks.external, s);
     if (cudaMemsetAsync(L.misc + 2, 0, sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
-    k_gather_units<<<sms * ctas_per_sm, kGatherWarps * 32, 0, s>>>(gz, L.runs, L.vals[cur], L.bstart, L.bend,
-                                                                  L.ustart, L.unit_brick, L.misc + 0, G, L.upart,
-                                                                  L.misc + 2);
+    const int grid = sms * ctas_per_sm;
+    const PoseOut po{L.rpart, slots};
+    if (!pose_part)
+        launch_units<float, false>(gz, L, cur, G, vol, po, grid, s);
+    else if (vd->dtype == DIFFUS_F32)
+        launch_units<float, true>(gz, L, cur, G, vol, po, grid, s);
+    else
+        launch_units<unsigned short, true>(gz, L, cur, G, vol, po, grid, s);
     record_mark(marks.reduce, marks.external, s);
     const size_t nv = (size_t)vd->nx * vd->ny * vd->nz;
     k_voxel_reduce<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(L.upart, L.ustart, L.ucount, G, grad_vol);
+    if (pose_part)
+        k_ray_pose<<<(unsigned)((n_rays + 127) / 128), 128, 0, s>>>(
+            L.rpart, slots, L.nrun, geo, (int)n_rays, (float)(1.0 / vd->sx), (float)(1.0 / vd->sy),
+            (float)(1.0 / vd->sz), pose_part);
     return launch_status();
 }
 

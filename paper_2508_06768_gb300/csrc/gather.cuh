@@ -21,6 +21,13 @@
 //  5. reduce: each voxel sums the partials of the units of the (up to 8)
 //             bricks whose cells touch it, in a fixed order.
 //
+// The same cell moments give the pose gradient (Section 2.5): inside a cell
+// the derivative of the trilinear form along each axis is a quadratic in the
+// sample index, so sum_k dL/dZ_k dZ/dx_a(k) and its depth-weighted twin
+// follow from the moments and the cell's 8 corners.  Each lane sums them over
+// its run and writes them at the run's slot; a per-ray pass adds a ray's runs
+// in slot order.  The adjoint march then samples values only.
+//
 // No floating-point atomics are used and every sum has a fixed order, so the
 // gradient is bitwise reproducible.
 #pragma once
@@ -42,14 +49,14 @@ struct GatherArgs {
 
 // Samples k0 .. k0+len-1 of one ray lie in cells of one brick.  The run
 // carries all a gather lane needs to walk it: the fixed-point position of
-// its first sample, the ray's step, and the offset of its first dL/dZ
-// value.
+// its first sample, the ray's step, the offset of its first dL/dZ value and
+// the index k0 of its first sample along the ray.
 struct alignas(16) Run {
     long long X, Y, Z;
     long long dX, dY, dZ;
     long long g_off;
     int len;
-    int pad;
+    int k0;
 };
 static_assert(sizeof(Run) == 64, "Run layout");
 
@@ -92,8 +99,11 @@ __device__ __forceinline__ int cell_of(long long X, int n)
     return X < 0 ? 0 : (hi > n - 2 ? n - 2 : hi);
 }
 
+template <bool POSE>
 struct GatherSmem {
     float acc[kGatherWarps][kBrickVox];
+    float vox[POSE ? kGatherWarps : 1][POSE ? kBrickVox : 1];   // the brick's volume values (pose terms)
+    float pose[POSE ? kGatherWarps : 1][6][32];                  // per-lane sums of the lane's run
 };
 
 // Adds one closed cell record per flagged lane into the warp's accumulator.
@@ -173,19 +183,48 @@ __device__ __forceinline__ void axis_cell(long long X, long long dX, int n, int 
 
 // Samples from X (inclusive) before the axis's cell or its clamping changes
 // (at most cap): the next crossing of a cell face, of 0 from below or of
-// n-1 from above.
+// n-1 from above.  A sample exactly at coordinate 0 forms a record of its
+// own: there the sampler's gradient along the axis is zero (the coordinate
+// is not strictly inside the volume), so every record is either wholly
+// strictly inside or wholly not, along each axis.
 __device__ __forceinline__ int axis_steps(long long X, long long dX, int n, int cap)
 {
     const long long top = (long long)(n - 1) << 32;
     if (X < 0) return dX > 0 ? ceil_div_fixed(-X, dX, cap) : cap;
     if (X >= top) return dX < 0 ? ceil_div_fixed(X - top + 1, -dX, cap) : cap;
+    if (X == 0 && dX != 0) return 1;
     const long long c = X >> 32;
     if (dX > 0) return ceil_div_fixed(((c + 1) << 32) - X, dX, cap);
-    if (dX < 0) return ceil_div_fixed(X - (c << 32) + 1, -dX, cap);
+    if (dX < 0) return ceil_div_fixed(X - (c << 32) + (c == 0 ? 0 : 1), -dX, cap);
     return cap;
 }
 
+// The derivative along one axis of the trilinear form, over a cell record,
+// as a quadratic p0 + p1 k + p2 k^2 in the record's sample index k.  D[i][j]
+// are the corner differences along the axis at the other two axes' corners
+// i (weight u + v k of corner 1) and j (weight w + t k of corner 1).
+__device__ __forceinline__ void axis_poly(float D00, float D10, float D01, float D11, float u, float v, float w,
+                                          float t, float &p0, float &p1, float &p2)
+{
+    const float h0 = D10 - D00, h1 = D11 - D01;
+    const float e00 = fmaf(h0, u, D00), e01 = h0 * v;    // j = 0: e00 + e01 k
+    const float e10 = fmaf(h1, u, D01), e11 = h1 * v;    // j = 1
+    const float f0 = e10 - e00, f1 = e11 - e01;
+    p0 = fmaf(f0, w, e00);
+    p1 = fmaf(f1, w, fmaf(f0, t, e01));
+    p2 = f1 * t;
+}
+
 constexpr int kGStepCap = 1 << 24;   // "no crossing within the run"
+
+// Pose-gradient sums of one run, written at the run's slot: component q
+// (T_x, T_y, T_z, U_x, U_y, U_z) at rpart[q * slots + slot], with
+// T_a = sum_k dL/dZ_k dZ/dx_a(k) and U_a = sum_k dL/dZ_k (k + 1/2) dZ/dx_a(k)
+// in voxel-index units (k along the ray).
+struct PoseOut {
+    float *rpart;
+    size_t slots;
+};
 
 // Gather the runs [q0, q1) of one brick (first cell (bx0, by0, bz0)) into
 // this warp's 9^3 accumulator.  Each lane walks one run, one cell at a
@@ -196,18 +235,25 @@ constexpr int kGStepCap = 1 << 24;   // "no crossing within the run"
 // moments, and the corner sums are formed once per cell.  The warp then
 // flushes the step's cell records together.  A lane whose run ends takes
 // the next run in order, so every decision depends only on the data and
-// the sums have a fixed order.
+// the sums have a fixed order.  With POSE the lane also sums the run's
+// pose-gradient terms from the same moments and the cell's corner values.
+template <bool POSE>
 __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const uint32_t *__restrict__ order,
                                             uint32_t q0, uint32_t q1, const float *__restrict__ gzbuf,
-                                            const GatherArgs &G, int bx0, int by0, int bz0, GatherSmem &sm, int w)
+                                            const GatherArgs &G, int bx0, int by0, int bz0, GatherSmem<POSE> &sm,
+                                            int w, const PoseOut &po)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     float *acc = sm.acc[w];
+    const float *vox = sm.vox[POSE ? w : 0];
     long long X = 0, Y = 0, Z = 0, dX = 0, dY = 0, dZ = 0;
     const float *g = gzbuf;
     int left = 0;                 // samples left in the lane's run
     int cx = 0, cy = 0, cz = 0;   // samples left before each axis's next crossing (0: recompute)
+    uint32_t slot = 0;            // the run's slot (pose output)
+    int kc = 0;                   // index along the ray of the next sample
+    float(*pz)[32] = sm.pose[POSE ? w : 0];
     uint32_t next = q0;           // next unassigned run (warp-uniform)
     // lane i holds the index of run next + i, loaded one refill ahead
     uint32_t pre = next + lane < q1 ? order[next + lane] : 0u;
@@ -229,6 +275,12 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
                 g = gzbuf + run.g_off;
                 left = run.len;
                 cx = cy = cz = 0;
+                if (POSE) {
+                    slot = idx;
+                    kc = run.k0;
+#pragma unroll
+                    for (int q = 0; q < 6; q++) pz[q][lane] = 0.0f;
+                }
             }
             next += __popc(idles);
             pre = next + lane < q1 ? order[next + lane] : 0u;
@@ -284,6 +336,32 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
         }
         const bool has = len > 0;
         const int cell = (ix - bx0) | ((iy - by0) << 3) | ((iz - bz0) << 6);
+        if (POSE && has) {
+            // the cell's 8 corner values, from the brick copy in shared memory
+            const int base = ((iz - bz0) * kBrickV + (iy - by0)) * kBrickV + (ix - bx0);
+            float c[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) c[q] = vox[base + ((q >> 2) * kBrickV + ((q >> 1) & 1)) * kBrickV + (q & 1)];
+            // per axis: sum_k g_k dZ/dx_a(k) = p0 M0 + p1 M1 + p2 M2 and the
+            // k-weighted sum p0 M1 + p1 M2 + p2 M3, zero where the coordinate
+            // is not strictly inside (0, n-1)
+            float p[3][3];
+            axis_poly(c[1] - c[0], c[3] - c[2], c[5] - c[4], c[7] - c[6], uy, vy, uz, vz, p[0][0], p[0][1], p[0][2]);
+            axis_poly(c[2] - c[0], c[3] - c[1], c[6] - c[4], c[7] - c[5], ux, vx, uz, vz, p[1][0], p[1][1], p[1][2]);
+            axis_poly(c[4] - c[0], c[5] - c[1], c[6] - c[2], c[7] - c[3], ux, vx, uy, vy, p[2][0], p[2][1], p[2][2]);
+            const bool in[3] = {X > 0 && (int)(X >> 32) < G.nx - 1, Y > 0 && (int)(Y >> 32) < G.ny - 1,
+                                Z > 0 && (int)(Z >> 32) < G.nz - 1};
+            const float kh = (float)kc + 0.5f;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const float Ta = fmaf(p[a][2], M2, fmaf(p[a][1], M1, p[a][0] * M0));
+                const float Wa = fmaf(p[a][2], M3, fmaf(p[a][1], M2, p[a][0] * M1));
+                if (in[a]) {
+                    pz[a][lane] += Ta;
+                    pz[3 + a][lane] += fmaf(kh, Ta, Wa);
+                }
+            }
+        }
         if (has) {
             X += (long long)len * dX;
             Y += (long long)len * dY;
@@ -293,6 +371,13 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
             cx -= len;
             cy -= len;
             cz -= len;
+            if (POSE) {
+                kc += len;
+                if (left == 0) {
+#pragma unroll
+                    for (int q = 0; q < 6; q++) po.rpart[(size_t)q * po.slots + slot] = pz[q][lane];
+                }
+            }
         }
         flush_records(has, cell, v, acc, lane, lt);
     }

@@ -160,8 +160,11 @@ inline void record_mark(cudaEvent_t e, bool external, cudaStream_t s)
 
 MarchArgs make_march_args(const diffus_volume_desc *vd, const diffus_fan *fan, const diffus_params *prm);
 size_t gather_workspace_bytes(const diffus_volume_desc *vd, long long n_rays, double max_path_mm);
-int launch_gather(const diffus_volume_desc *vd, const RayGeo *geo, long long n_rays, double max_path_mm,
-                  const float *gz, const long long *gz_off, void *ws, uint32_t *status, float *grad_vol,
-                  int ctas_per_sm, cudaStream_t s, const GatherMarks &marks = GatherMarks());
+// Volume gradient from dL/dZ (and, when pose_part is non-NULL, each ray's
+// six pose-gradient terms from the same brick walk, into pose_part[6 r]).
+int launch_gather(const diffus_volume_desc *vd, const void *vol, const RayGeo *geo, long long n_rays,
+                  double max_path_mm, const float *gz, const long long *gz_off, void *ws, uint32_t *status,
+                  float *grad_vol, double *pose_part, int ctas_per_sm, cudaStream_t s,
+                  const GatherMarks &marks = GatherMarks());
 
 }  // namespace dfs

@@ -10,8 +10,10 @@
 // keeps only the scan carry at each segment start (16 bytes per segment),
 // then segments are revisited from the last to the first.
 //
-// Outputs per ray: dL/dZ_k for the S+1 samples (for the volume gather) and
-// the ray's contribution to dL/dpose (FP64 sums of per-segment FP32 sums).
+// Outputs per ray: dL/dZ_k for the S+1 samples (for the volume gather) and,
+// with POSE, the ray's contribution to dL/dpose (FP64 sums of per-segment
+// FP32 sums).  Without POSE the march samples values only; the brick gather
+// then forms the pose gradient from dL/dZ and the cells' corners.
 #pragma once
 
 #include "march.cuh"
@@ -20,10 +22,11 @@ namespace dfs {
 
 constexpr int kBwdPad = 289;   // smem_idx(256) + 1
 
+template <bool POSE>
 struct BwdSmem {
     float zr[kBwdPad], dz[kBwdPad];   // samples base .. base+256 (zref + dz form)
-    float gx[kBwdPad], gy[kBwdPad], gz[kBwdPad];
-    double acc[6];                    // the ray's pose-gradient sums (lane 0)
+    float gx[POSE ? kBwdPad : 1], gy[POSE ? kBwdPad : 1], gz[POSE ? kBwdPad : 1];   // dZ/dp (POSE)
+    double acc[POSE ? 6 : 1];         // the ray's pose-gradient sums (lane 0)
 };
 
 // Echo of one interface and its partial derivatives with respect to the
@@ -50,10 +53,10 @@ __device__ __forceinline__ EchoGrad echo_grad(float b0, float b1, float D, float
 // carries into ckpt, so the recording sweep is skipped.
 // mrow: speckle factors written by the forward of the same call (nullable;
 // recomputed from Philox when absent).
-template <typename T>
+template <typename T, bool POSE>
 __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, const RayGeo &rg,
                               const float *__restrict__ gy_row, float *__restrict__ gz_row,
-                              double *__restrict__ pose_part, float4 *__restrict__ ckpt, BwdSmem &sm,
+                              double *__restrict__ pose_part, float4 *__restrict__ ckpt, BwdSmem<POSE> &sm,
                               bool have_ckpt = false, const float *__restrict__ mrow = nullptr)
 {
     const int lane = threadIdx.x & 31;
@@ -94,7 +97,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
     float carry_gz1 = 0.0f;                       // dL/dZ of sample base+256 from interface base+256
     float czr = 0.0f, cdz = 0.0f, cg0 = 0.0f, cg1 = 0.0f, cg2 = 0.0f;   // sample base+256
     double *acc = sm.acc;
-    if (lane == 0)
+    if (POSE && lane == 0)
         for (int q = 0; q < 6; q++) acc[q] = 0.0;
     const float ds = rg.ds;
 
@@ -109,28 +112,40 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
             int p = t * kWarp + lane;
             int k = base + p;
             float zr = 0.0f, dz = 0.0f, g3[3] = {0.0f, 0.0f, 0.0f};
-            if (k <= S) sample_z<T, true>(vol, A.g, X, Y, Z, zr, dz, g3);
+            if (k <= S) {
+                if (POSE)
+                    sample_z<T, true>(vol, A.g, X, Y, Z, zr, dz, g3);
+                else
+                    sample_z<T, false>(vol, A.g, X, Y, Z, zr, dz);
+            }
             X += sX;
             Y += sY;
             Z += sZ;
             int o = smem_idx(p);
-            sm.zr[o] = zr; sm.dz[o] = dz; sm.gx[o] = g3[0]; sm.gy[o] = g3[1]; sm.gz[o] = g3[2];
+            sm.zr[o] = zr; sm.dz[o] = dz;
+            if (POSE) { sm.gx[o] = g3[0]; sm.gy[o] = g3[1]; sm.gz[o] = g3[2]; }
         }
         if (lane == 0) {
             if (s == nseg - 1 && base + kSeg <= S) {
                 long long X, Y, Z;
                 float g3[3];
                 sample_pos(rg, base + kSeg, X, Y, Z);
-                sample_z<T, true>(vol, A.g, X, Y, Z, czr, cdz, g3);
-                cg0 = g3[0]; cg1 = g3[1]; cg2 = g3[2];
+                if (POSE) {
+                    sample_z<T, true>(vol, A.g, X, Y, Z, czr, cdz, g3);
+                    cg0 = g3[0]; cg1 = g3[1]; cg2 = g3[2];
+                } else {
+                    sample_z<T, false>(vol, A.g, X, Y, Z, czr, cdz);
+                }
             }
             int o = smem_idx(kSeg);
-            sm.zr[o] = czr; sm.dz[o] = cdz; sm.gx[o] = cg0; sm.gy[o] = cg1; sm.gz[o] = cg2;
+            sm.zr[o] = czr; sm.dz[o] = cdz;
+            if (POSE) { sm.gx[o] = cg0; sm.gy[o] = cg1; sm.gz[o] = cg2; }
         }
         __syncwarp();
         {   // carry the first sample of this segment to the earlier one
             int o = smem_idx(0);
-            czr = sm.zr[o]; cdz = sm.dz[o]; cg0 = sm.gx[o]; cg1 = sm.gy[o]; cg2 = sm.gz[o];
+            czr = sm.zr[o]; cdz = sm.dz[o];
+            if (POSE) { cg0 = sm.gx[o]; cg1 = sm.gy[o]; cg2 = sm.gz[o]; }
         }
 
         // B': reflection coefficients of this lane's chunk and the forward scan
@@ -243,6 +258,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
         float n_last = 0.0f;     // Z2-role contribution of interface i0+7 to sample i0+8
         float c_first = 0.0f;    // Z1-role contribution of interface i0 to sample i0
         auto add_pose = [&](int k, int o, float G) {
+            if (!POSE) return;
             const float gx = sm.gx[o], gyv = sm.gy[o], gzv = sm.gz[o];
             const float sk = ((float)k + 0.5f) * ds;
             a[0] = fmaf(G, gx, a[0]);
@@ -314,16 +330,18 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
             add_pose(0, smem_idx(0), c_first);
         }
         carry_gz1 = __shfl_sync(0xffffffffu, c_first, 0);
+        if (POSE) {
 #pragma unroll
-        for (int q = 0; q < 6; q++) {
-            float v = a[q];
+            for (int q = 0; q < 6; q++) {
+                float v = a[q];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-            if (lane == 0) acc[q] += (double)v;
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if (lane == 0) acc[q] += (double)v;
+            }
         }
         __syncwarp();
     }
-    if (lane == 0) {
+    if (POSE && lane == 0) {
         pose_part[0] = acc[0];
         pose_part[1] = acc[1];
         pose_part[2] = acc[2];

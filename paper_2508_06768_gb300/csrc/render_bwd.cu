@@ -1,5 +1,7 @@
 // Single-pose backward entry point: blur transpose -> adjoint march ->
-// pose reduction -> atomic-free brick gather of the volume gradient.
+// atomic-free brick gather of the volume gradient (with the per-ray pose
+// terms) -> pose reduction.  Without a volume gradient the adjoint march
+// forms the pose terms itself and no gather runs.
 #include "host.hpp"
 #include "march_bwd.cuh"
 
@@ -14,7 +16,7 @@ int check_common(const void *vol, const diffus_volume_desc *vd, const float *pos
 
 constexpr int kWarpsBwd = 4;
 
-template <typename T>
+template <typename T, bool POSE>
 __global__ void __launch_bounds__(kWarpsBwd * 32) k_march_bwd(const T *__restrict__ vol, MarchArgs A,
                                                               const RayGeo *__restrict__ geo, int n_rays,
                                                               const float *__restrict__ gy,
@@ -25,12 +27,12 @@ __global__ void __launch_bounds__(kWarpsBwd * 32) k_march_bwd(const T *__restric
                                                               float4 *__restrict__ ckpt,
                                                               const long long *__restrict__ ckpt_off)
 {
-    __shared__ BwdSmem sm[kWarpsBwd];
+    __shared__ BwdSmem<POSE> sm[kWarpsBwd];
     const int w = threadIdx.x >> 5;
     const int j = blockIdx.x * kWarpsBwd + w;
     if (j >= n_rays) return;
     RayGeo rg = geo[j];
-    march_bwd_ray<T>(vol, A, rg, gy + row_off[j], gz + gz_off[j], pose_part + 6 * (size_t)j, ckpt + ckpt_off[j],
+    march_bwd_ray<T, POSE>(vol, A, rg, gy + row_off[j], gz + gz_off[j], pose_part + 6 * (size_t)j, ckpt + ckpt_off[j],
                      sm[w]);
 }
 
@@ -100,6 +102,27 @@ static BwdLayout bwd_layout(void *ws, const diffus_volume_desc *vd, const diffus
     return L;
 }
 
+template <typename T, bool POSE>
+static void launch_march_bwd_t(const void *vol, const MarchArgs &A, const BwdLayout &L, int n, const float *gy,
+                               int grid, cudaStream_t s)
+{
+    k_march_bwd<T, POSE><<<grid, kWarpsBwd * 32, 0, s>>>((const T *)vol, A, L.geo, n, gy, L.row_off, L.gz, L.gz_off,
+                                                         L.part, L.ckpt, L.ck_off);
+}
+
+static int launch_march_bwd(const void *vol, int dtype, bool pose, const MarchArgs &A, const BwdLayout &L, int n,
+                            const float *gy, int grid, cudaStream_t s)
+{
+    if (dtype == DIFFUS_F32) {
+        if (pose) launch_march_bwd_t<float, true>(vol, A, L, n, gy, grid, s);
+        else launch_march_bwd_t<float, false>(vol, A, L, n, gy, grid, s);
+    } else {
+        if (pose) launch_march_bwd_t<unsigned short, true>(vol, A, L, n, gy, grid, s);
+        else launch_march_bwd_t<unsigned short, false>(vol, A, L, n, gy, grid, s);
+    }
+    return launch_status();
+}
+
 size_t bwd_workspace_bytes(const diffus_volume_desc *vd, const diffus_fan *fan, const diffus_params *prm)
 {
     return bwd_layout(nullptr, vd, fan, prm).bytes;
@@ -142,16 +165,12 @@ extern "C" int diffus_render_bwd(const void *vol, const diffus_volume_desc *vd, 
     }
     MarchArgs A = make_march_args(vd, fan, prm);
     int grid = (n + kWarpsBwd - 1) / kWarpsBwd;
-    if (vd->dtype == DIFFUS_F32)
-        k_march_bwd<float><<<grid, kWarpsBwd * 32, 0, s>>>((const float *)vol, A, L.geo, n, gy, L.row_off, L.gz,
-                                                           L.gz_off, L.part, L.ckpt, L.ck_off);
-    else
-        k_march_bwd<unsigned short><<<grid, kWarpsBwd * 32, 0, s>>>((const unsigned short *)vol, A, L.geo, n, gy,
-                                                                    L.row_off, L.gz, L.gz_off, L.part, L.ckpt,
-                                                                    L.ck_off);
-    if ((rc = launch_status())) return rc;
+    const bool march_pose = grad_pose && !grad_vol;
+    if ((rc = launch_march_bwd(vol, vd->dtype, march_pose, A, L, n, gy, grid, s))) return rc;
+    if (grad_vol &&
+        (rc = launch_gather(vd, vol, L.geo, n, fan->depth_mm, L.gz, L.gz_off, L.gather_ws, status, grad_vol,
+                            grad_pose ? L.part : nullptr, 8, s)))
+        return rc;
     if (grad_pose) k_pose_reduce<<<1, 32, 0, s>>>(L.part, L.ray0, 1, grad_pose);
-    if (grad_vol)
-        rc = launch_gather(vd, L.geo, n, fan->depth_mm, L.gz, L.gz_off, L.gather_ws, status, grad_vol, 8, s);
-    return rc ? rc : launch_status();
+    return launch_status();
 }

@@ -40,16 +40,18 @@ def gpu_render(vol, pose, fan, params, pose_ctr=0, bf16=False):
     return img.cpu().numpy().astype(np.float64), valid.cpu().numpy(), status.cpu().numpy().view(np.uint32)
 
 
-def gpu_grad(vol, pose, fan, params, G, pose_ctr=0, bf16=False):
+def gpu_grad(vol, pose, fan, params, G, pose_ctr=0, bf16=False, want_vol=True):
     import torch
     from paper_2508_06768_gb300 import binding as B
     dt = torch.bfloat16 if bf16 else torch.float32
     v = torch.from_numpy(np.ascontiguousarray(vol.data)).to("cuda").to(dt)
     p = torch.tensor(np.asarray(pose, dtype=np.float32), device="cuda")
     g = torch.from_numpy(np.ascontiguousarray(G, dtype=np.float32)).to("cuda")
-    gvol, gpose, status = B.render_bwd(v, vol.spacing, vol.origin, p, fan, params, g, pose_ctr=pose_ctr)
+    gvol, gpose, status = B.render_bwd(v, vol.spacing, vol.origin, p, fan, params, g, pose_ctr=pose_ctr,
+                                       want_vol=want_vol)
     torch.cuda.synchronize()
-    return gvol.cpu().numpy().astype(np.float64), gpose.cpu().numpy().astype(np.float64)
+    gv = gvol.cpu().numpy().astype(np.float64) if want_vol else None
+    return gv, gpose.cpu().numpy().astype(np.float64)
 
 
 def bf16_round(a):

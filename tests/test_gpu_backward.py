@@ -78,6 +78,39 @@ def test_tiny_volume_every_voxel():
     _check(vol, pose, fan, prm, G)
 
 
+def _case(name):
+    if name == "small":
+        vol, pose, fan, prm = I.workload_small()
+        return vol, pose, fan, prm.with_(mode=1)
+    if name == "clamped":   # rays leave the volume: clamped samples, zero gradient along those axes
+        vol = I.small_phantom(n=40, seed=7)
+        fan = I.Fan(19, 300 + 7, math.radians(75), 70.0, 6.0, 0.7)
+        pose = np.array([12.0, 30.0, -3.0, 0.2, -0.4, 0.7], dtype=np.float32)
+        return vol, pose, fan, I.Params(seed=5, mode=1, gshift=1)
+    rng = np.random.default_rng(4)
+    vol = I.Volume((1.5 + 0.2 * rng.random((3, 4, 5))).astype(np.float32), (1.0, 0.8, 1.3), (0.2, -0.1, 0.3))
+    fan = I.Fan(5, 61, 0.9, 6.0, 5.0, 0.5)
+    pose = np.array([1.5, 1.2, -1.0, 0.3, 0.2, 0.5], dtype=np.float32)
+    return vol, pose, fan, I.Params(mode=1, seed=3)
+
+
+@pytest.mark.parametrize("name", ["small", "clamped", "tiny"])
+def test_pose_gradient_with_and_without_volume_gradient(name):
+    # With a volume gradient the brick gather forms the pose terms from the
+    # cells' corners; without one the adjoint march samples dZ/dp itself.
+    # Both against the oracle, and against each other.
+    vol, pose, fan, prm = _case(name)
+    G = _loss_weights(vol, pose, fan, prm, seed=13) if name != "tiny" else I.random_weights((5, 61), 9)
+    _, rpose = oracle.render_grad(vol, pose, fan, prm, G.astype(np.float64))
+    _, gp_full = gpu_grad(vol, pose, fan, prm, G)
+    gv, gp_only = gpu_grad(vol, pose, fan, prm, G, want_vol=False)
+    assert gv is None
+    e_full, e_only = _rel(gp_full, rpose), _rel(gp_only, rpose)
+    print("%s: pose grad err with gather %.3e, march only %.3e" % (name, e_full, e_only))
+    assert e_full <= GRAD_TOL and e_only <= GRAD_TOL, (e_full, e_only)
+    assert _rel(gp_full, gp_only) <= 2 * GRAD_TOL
+
+
 def test_finite_differences_of_the_cuda_forward():
     # Central differences (h = 1e-3) of L = sum(G * image) on the CUDA path,
     # against the same differences of the FP64 oracle.  Trilinear sampling is

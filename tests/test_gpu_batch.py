@@ -62,6 +62,33 @@ def test_batch_equals_single_pose_bitwise():
     assert np.linalg.norm(gb - gvol_sum) <= 1e-6 * np.linalg.norm(gvol_sum)
 
 
+def test_pose_only_batch_call():
+    # grad_vol = NULL: the adjoint march forms the pose terms (no gather);
+    # bitwise equal to pose-only single-pose calls, and close to the pose
+    # gradient that the gather forms when the volume gradient is asked too
+    import torch
+    from paper_2508_06768_gb300 import binding as B
+    vol, poses, fans, prm = _workload(seed=23)
+    r = _renderer(vol, fans, prm)
+    Gs = [I.random_weights((f.n_rays, f.n_samples), 300 + p) for p, f in enumerate(fans)]
+    G = torch.from_numpy(np.concatenate([g.ravel() for g in Gs])).cuda()
+    pd = torch.from_numpy(poses).cuda()
+    r.run(pd, G)
+    full = r.grad_poses.clone()
+    gp = torch.empty_like(full)
+    B.render_batch(r.volume, r.spacing, r.origin, pd, r.plan_host, r.plan_dev, r.params, r.images, r.workspace,
+                   ray_valid=r.ray_valid, grad_images=G, grad_vol=None, grad_poses=gp, status=r.status)
+    torch.cuda.synchronize()
+    v = torch.from_numpy(vol.data).cuda()
+    for p in range(len(fans)):
+        pt = torch.from_numpy(np.asarray(poses[p], np.float32)).cuda()
+        _, gs, _ = B.render_bwd(v, vol.spacing, vol.origin, pt, fans[p], prm, torch.from_numpy(Gs[p]).cuda(),
+                                pose_ctr=p, want_vol=False)
+        assert np.array_equal(gp[p].cpu().numpy(), gs.cpu().numpy()), p
+        a, b = gp[p].cpu().numpy().astype(np.float64), full[p].cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(a - b) <= 2 * GRAD_TOL * np.linalg.norm(b), (p, a, b)
+
+
 def test_batch_vs_oracle():
     import torch
     vol, poses, fans, prm = _workload(mode=0)
