@@ -69,7 +69,7 @@ enum { DIFFUS_STATUS_QUEUE = 1u, DIFFUS_STATUS_PLAN = 2u };
 
 /* Volume geometry.  dtype is DIFFUS_F32 or DIFFUS_BF16. */
 typedef struct {
-    int32_t nx, ny, nz;
+    int32_t nx, ny, nz;         /* voxels per axis: each in [2, 65535], nx ny nz < 2^31 (else DIFFUS_E_DIMS) */
     int32_t dtype;
     double sx, sy, sz;          /* spacing, mm (> 0) */
     double ox, oy, oz;          /* centre of voxel (0,0,0), mm */

@@ -107,6 +107,7 @@ int64_t count_tiles(const diffus_fan *fans, int P)
 
 struct BatchLayout {
     RayGeo *geo;
+    PoseFrame *frames;
     float *y;        // pre-blur rows (blur on)
     unsigned *counter;
     float *gy;       // blur transpose of grad_images (blur on)
@@ -124,6 +125,7 @@ BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc
     Carve c(ws);
     BatchLayout L;
     L.geo = c.take<RayGeo>((size_t)H.total_rays);
+    L.frames = c.take<PoseFrame>((size_t)H.P);
     L.counter = c.take<unsigned>(4);
     L.y = blur ? c.take<float>((size_t)H.total_img) : nullptr;
     L.fwd_bytes = c.used;
@@ -146,7 +148,7 @@ struct BatchDev {
     int64_t total_rays;
 };
 
-__global__ void k_batch_setup(const float *__restrict__ poses, BatchDev B, VolPlace vp, RayGeo *__restrict__ geo)
+__global__ void k_batch_setup(const PoseFrame *__restrict__ frames, BatchDev B, VolPlace vp, RayGeo *__restrict__ geo)
 {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= B.total_rays) return;
@@ -154,7 +156,7 @@ __global__ void k_batch_setup(const float *__restrict__ poses, BatchDev B, VolPl
     const PlanPose pp = B.pose[p];
     FanDev fd{pp.n_rays, pp.S, pp.fov, pp.depth};
     RayGeo rg;
-    setup_ray(poses + 6 * (size_t)p, p, B.ray_j[r], fd, vp, rg);
+    setup_ray(frames[p], p, B.ray_j[r], fd, vp, rg);
     geo[r] = rg;
 }
 
@@ -514,7 +516,8 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     if (status && cudaMemsetAsync(status, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
     if (cudaMemsetAsync(L.counter, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
     mark(DIFFUS_TR_START);
-    k_batch_setup<<<(unsigned)((H.total_rays + 127) / 128), 128, 0, s>>>(poses, B, make_place(vd), L.geo);
+    k_pose_frames<<<(H.P + 127) / 128, 128, 0, s>>>(poses, H.P, L.frames);
+    k_batch_setup<<<(unsigned)((H.total_rays + 127) / 128), 128, 0, s>>>(L.frames, B, make_place(vd), L.geo);
     mark(DIFFUS_TR_MARCH_FWD);
 
     // march parameters shared by all poses (a^2 comes from the pose table)

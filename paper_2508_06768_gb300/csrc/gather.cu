@@ -297,39 +297,51 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
     }
 }
 
-// Each voxel: sum over the bricks whose cells touch it (brick of cell v and,
-// on a brick face, of cell v-1), units in order.
+// The bricks whose cells touch voxel v along one axis, with v's index
+// inside each brick's 9 voxels: the brick of cell v-1 when v is on its far
+// face (or v is the last voxel), then the brick of cell v.  At most two.
+__device__ __forceinline__ int voxel_bricks(int v, int n, int (&b)[2], int (&l)[2])
+{
+    int k = 0;
+    if (v >= 1) {
+        const int c = (v - 1) >> 3;
+        if (!(v <= n - 2 && c == (v >> 3))) {
+            b[k] = c;
+            l[k] = v - c * kBrick;
+            k++;
+        }
+    }
+    if (v <= n - 2) {
+        b[k] = v >> 3;
+        l[k] = v - (v >> 3) * kBrick;
+        k++;
+    }
+    return k;
+}
+
+// Each voxel: sum over the bricks whose cells touch it (z outer, then y,
+// then x; on each axis the lower brick first), units in order.  Grid:
+// x over blocks of threads, y and z one block row per voxel row.
 __global__ void k_voxel_reduce(const float *__restrict__ upart, const uint32_t *__restrict__ ustart,
                                const uint32_t *__restrict__ ucount, GatherArgs G, float *__restrict__ grad_vol)
 {
-    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t nv = (size_t)G.nx * G.ny * G.nz;
-    if (v >= nv) return;
-    const int vx = (int)(v % G.nx), vy = (int)((v / G.nx) % G.ny), vz = (int)(v / ((size_t)G.nx * G.ny));
+    const int vx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int vy = blockIdx.y, vz = blockIdx.z;
+    if (vx >= G.nx) return;
+    int bx[2], lx[2], by[2], ly[2], bz[2], lz[2];
+    const int kx = voxel_bricks(vx, G.nx, bx, lx);
+    const int ky = voxel_bricks(vy, G.ny, by, ly);
+    const int kz = voxel_bricks(vz, G.nz, bz, lz);
     float s = 0.0f;
-    for (int dz = 1; dz >= 0; dz--) {
-        int cz = vz - dz;                         // a cell of the brick, touching voxel vz
-        if (cz < 0 || cz > G.nz - 2) continue;
-        int bz = cz / kBrick;
-        if (dz == 1 && bz == vz / kBrick && vz <= G.nz - 2) continue;   // same brick counted with dz = 0
-        for (int dy = 1; dy >= 0; dy--) {
-            int cy = vy - dy;
-            if (cy < 0 || cy > G.ny - 2) continue;
-            int by = cy / kBrick;
-            if (dy == 1 && by == vy / kBrick && vy <= G.ny - 2) continue;
-            for (int dx = 1; dx >= 0; dx--) {
-                int cx = vx - dx;
-                if (cx < 0 || cx > G.nx - 2) continue;
-                int bx = cx / kBrick;
-                if (dx == 1 && bx == vx / kBrick && vx <= G.nx - 2) continue;
-                const int b = (bz * G.nby + by) * G.nbx + bx;
-                const int li = ((vz - bz * kBrick) * kBrickV + (vy - by * kBrick)) * kBrickV + (vx - bx * kBrick);
+    for (int iz = 0; iz < kz; iz++)
+        for (int iy = 0; iy < ky; iy++)
+            for (int ix = 0; ix < kx; ix++) {
+                const int b = (bz[iz] * G.nby + by[iy]) * G.nbx + bx[ix];
+                const int li = (lz[iz] * kBrickV + ly[iy]) * kBrickV + lx[ix];
                 const uint32_t u0 = ustart[b], u1 = u0 + ucount[b];
                 for (uint32_t u = u0; u < u1; u++) s += upart[(size_t)u * kBrickVox + li];
             }
-        }
-    }
-    grad_vol[v] = s;
+    grad_vol[((size_t)vz * G.ny + vy) * G.nx + vx] = s;
 }
 
 // Pose-gradient terms of each ray from its runs' sums, added in slot order
@@ -530,8 +542,8 @@ int launch_gather(const diffus_volume_desc *vd, const void *vol, const RayGeo *g
     else
         launch_units<unsigned short, true>(gz, L, cur, G, vol, po, grid, s);
     record_mark(marks.reduce, marks.external, s);
-    const size_t nv = (size_t)vd->nx * vd->ny * vd->nz;
-    k_voxel_reduce<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(L.upart, L.ustart, L.ucount, G, grad_vol);
+    k_voxel_reduce<<<dim3((unsigned)((vd->nx + 127) / 128), (unsigned)vd->ny, (unsigned)vd->nz), 128, 0, s>>>(
+        L.upart, L.ustart, L.ucount, G, grad_vol);
     if (pose_part)
         k_ray_pose<<<(unsigned)((n_rays + 127) / 128), 128, 0, s>>>(
             L.rpart, slots, L.nrun, geo, (int)n_rays, (float)(1.0 / vd->sx), (float)(1.0 / vd->sy),

@@ -21,6 +21,7 @@ inline int check_vol(const diffus_volume_desc *vd)
     if (!vd) return DIFFUS_E_NULL;
     if (vd->dtype != DIFFUS_F32 && vd->dtype != DIFFUS_BF16) return DIFFUS_E_DTYPE;
     if (vd->nx < 2 || vd->ny < 2 || vd->nz < 2) return DIFFUS_E_DIMS;
+    if (vd->nx > 65535 || vd->ny > 65535 || vd->nz > 65535) return DIFFUS_E_DIMS;   // grid rows of per-voxel kernels
     // 32-bit voxel offsets
     if ((double)vd->nx * vd->ny * vd->nz >= 2147483647.0) return DIFFUS_E_DIMS;
     if (!(vd->sx > 0 && vd->sy > 0 && vd->sz > 0)) return DIFFUS_E_PARAM;

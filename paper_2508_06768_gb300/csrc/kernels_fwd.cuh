@@ -49,44 +49,74 @@ __device__ __forceinline__ long long to_fixed(double x)
     return __double2ll_rn(x * 4294967296.0);
 }
 
-// Geometry of ray `ray` of pose `pose_idx` (Section 2.4): FP64 direction and
-// fixed-point positions, exactly t + (k + 1/2) ds u in voxel coordinates.
-__device__ __forceinline__ void setup_ray(const float *__restrict__ pose6, int pose_idx, int ray,
-                                          const FanDev &fan, const VolPlace &vp, RayGeo &out)
+// What the rays of one pose need from it (Section 2.4): columns 0 and 2 of
+// R and of each dR/dr_q (a fan direction d = (sin th, 0, cos th) has no
+// y component) and the translation, in FP64.  One thread per pose computes
+// them, so the per-ray setup has a single sincos.
+struct PoseFrame {
+    double Rc[3][2];
+    double dRc[3][3][2];
+    double t[3];
+};
+
+__device__ __forceinline__ void pose_frame(const float *__restrict__ pose6, PoseFrame &f)
 {
-    double r[3] = {(double)pose6[3], (double)pose6[4], (double)pose6[5]};
-    double t[3] = {(double)pose6[0], (double)pose6[1], (double)pose6[2]};
+    const double r[3] = {(double)pose6[3], (double)pose6[4], (double)pose6[5]};
     double R[3][3], dR[3][3][3];
     rotation_zyx(r, R, dR);
+    for (int i = 0; i < 3; i++) {
+        f.Rc[i][0] = R[i][0];
+        f.Rc[i][1] = R[i][2];
+        for (int q = 0; q < 3; q++) {
+            f.dRc[q][i][0] = dR[q][i][0];
+            f.dRc[q][i][1] = dR[q][i][2];
+        }
+        f.t[i] = (double)pose6[i];
+    }
+}
+
+static __global__ void k_pose_frames(const float *__restrict__ poses, int P, PoseFrame *__restrict__ frames)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P) return;
+    PoseFrame f;
+    pose_frame(poses + 6 * (size_t)p, f);
+    frames[p] = f;
+}
+
+// Geometry of ray `ray` of pose `pose_idx` (Section 2.4): FP64 direction and
+// fixed-point positions, exactly t + (k + 1/2) ds u in voxel coordinates.
+__device__ __forceinline__ void setup_ray(const PoseFrame &f, int pose_idx, int ray, const FanDev &fan,
+                                          const VolPlace &vp, RayGeo &out)
+{
     double th = fan.n_rays > 1 ? -0.5 * fan.fov + fan.fov * (double)ray / (double)(fan.n_rays - 1) : 0.0;
     double st, ct;
     sincos(th, &st, &ct);
-    double d[3] = {st, 0.0, ct};
     double u[3];
-    for (int i = 0; i < 3; i++) u[i] = R[i][0] * d[0] + R[i][1] * d[1] + R[i][2] * d[2];
+    for (int i = 0; i < 3; i++) u[i] = f.Rc[i][0] * st + f.Rc[i][1] * ct;
     double ds = fan.depth / (double)fan.S;
     double sp[3] = {vp.sx, vp.sy, vp.sz}, org[3] = {vp.ox, vp.oy, vp.oz};
     for (int i = 0; i < 3; i++) {
-        double x0 = (t[i] + 0.5 * ds * u[i] - org[i]) / sp[i];
+        double x0 = (f.t[i] + 0.5 * ds * u[i] - org[i]) / sp[i];
         double dx = ds * u[i] / sp[i];
         out.X0[i] = to_fixed(x0);
         out.DX[i] = __double2ll_rn(dx * 4294967296.0);
     }
     for (int q = 0; q < 3; q++)
-        for (int i = 0; i < 3; i++)
-            out.v[q][i] = (float)(dR[q][i][0] * d[0] + dR[q][i][1] * d[1] + dR[q][i][2] * d[2]);
+        for (int i = 0; i < 3; i++) out.v[q][i] = (float)(f.dRc[q][i][0] * st + f.dRc[q][i][1] * ct);
     out.pose = pose_idx;
     out.ray = ray;
     out.S = fan.S;
     out.ds = (float)ds;
 }
 
-static __global__ void k_ray_setup(const float *__restrict__ pose6, FanDev fan, VolPlace vp, RayGeo *__restrict__ geo)
+static __global__ void k_ray_setup(const PoseFrame *__restrict__ frame, FanDev fan, VolPlace vp,
+                                   RayGeo *__restrict__ geo)
 {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= fan.n_rays) return;
     RayGeo rg;
-    setup_ray(pose6, 0, j, fan, vp, rg);
+    setup_ray(*frame, 0, j, fan, vp, rg);
     geo[j] = rg;
 }
 

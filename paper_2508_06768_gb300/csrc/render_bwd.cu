@@ -72,6 +72,7 @@ static __global__ void k_offsets(long long *__restrict__ row_off, long long *__r
 
 struct BwdLayout {
     RayGeo *geo;
+    PoseFrame *frame;
     float *gy;
     float *gz;
     double *part;
@@ -89,6 +90,7 @@ static BwdLayout bwd_layout(void *ws, const diffus_volume_desc *vd, const diffus
     size_t n = (size_t)fan->n_rays, S = (size_t)fan->n_samples;
     size_t nseg = (S + kSeg - 1) / kSeg;
     L.geo = c.take<RayGeo>(n);
+    L.frame = c.take<PoseFrame>(1);
     L.gy = (prm->blur || prm->atten) ? c.take<float>(n * S) : nullptr;
     L.gz = c.take<float>(n * (S + 1));
     L.part = c.take<double>(6 * n);
@@ -149,7 +151,8 @@ extern "C" int diffus_render_bwd(const void *vol, const diffus_volume_desc *vd, 
     if (status && cudaMemsetAsync(status, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
     const int n = fan->n_rays, S = fan->n_samples;
     FanDev fd{n, S, fan->fov_rad, fan->depth_mm};
-    k_ray_setup<<<(n + 127) / 128, 128, 0, s>>>(pose, fd, make_place(vd), L.geo);
+    k_pose_frames<<<1, 32, 0, s>>>(pose, 1, L.frame);
+    k_ray_setup<<<(n + 127) / 128, 128, 0, s>>>(L.frame, fd, make_place(vd), L.geo);
     k_offsets<<<(n + 127) / 128, 128, 0, s>>>(L.row_off, L.gz_off, L.ck_off, L.ray0, n, S);
     const float *gy = grad_image;
     if (prm->blur) {

@@ -9,6 +9,7 @@ namespace {
 
 struct FwdLayout {
     RayGeo *geo;
+    PoseFrame *frame;
     float *y;       // pre-blur echo rows (only when blurring)
     size_t bytes;
 };
@@ -18,6 +19,7 @@ FwdLayout fwd_layout(void *ws, const diffus_fan *fan, const diffus_params *prm)
     Carve c(ws);
     FwdLayout L;
     L.geo = c.take<RayGeo>((size_t)fan->n_rays);
+    L.frame = c.take<PoseFrame>(1);
     L.y = prm->blur ? c.take<float>((size_t)fan->n_rays * fan->n_samples) : nullptr;
     L.bytes = c.used;
     return L;
@@ -62,11 +64,12 @@ int check_common(const void *vol, const diffus_volume_desc *vd, const float *pos
 // Launches ray setup and the march for one pose into `out` (pre-blur rows
 // when blurring follows).
 int launch_fwd_march(const void *vol, const diffus_volume_desc *vd, const float *pose, const diffus_fan *fan,
-                     const diffus_params *prm, RayGeo *geo, float *out, int32_t *ray_valid, uint32_t *status,
-                     cudaStream_t s)
+                     const diffus_params *prm, RayGeo *geo, PoseFrame *frame, float *out, int32_t *ray_valid,
+                     uint32_t *status, cudaStream_t s)
 {
     FanDev fd{fan->n_rays, fan->n_samples, fan->fov_rad, fan->depth_mm};
-    k_ray_setup<<<(fan->n_rays + 127) / 128, 128, 0, s>>>(pose, fd, make_place(vd), geo);
+    k_pose_frames<<<1, 32, 0, s>>>(pose, 1, frame);
+    k_ray_setup<<<(fan->n_rays + 127) / 128, 128, 0, s>>>(frame, fd, make_place(vd), geo);
     MarchArgs A = make_march_args(vd, fan, prm);
     int grid = (fan->n_rays + kWarpsFwd - 1) / kWarpsFwd;
 #define DFS_FWD(T, R) \
@@ -128,7 +131,7 @@ extern "C" int diffus_render_fwd(const void *vol, const diffus_volume_desc *vd, 
     cudaStream_t s = (cudaStream_t)stream;
     if (status && cudaMemsetAsync(status, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
     float *march_out = prm->blur ? L.y : image;
-    if ((rc = launch_fwd_march(vol, vd, pose, fan, prm, L.geo, march_out, ray_valid, status, s))) return rc;
+    if ((rc = launch_fwd_march(vol, vd, pose, fan, prm, L.geo, L.frame, march_out, ray_valid, status, s))) return rc;
     if (prm->atten && !prm->blur) {   // with blur the gain rides on the blur's output
         float hi, lo;
         gain_l2(attenuation_a(fan), hi, lo);

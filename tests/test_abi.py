@@ -45,6 +45,8 @@ def test_workspace_sizing_and_validation(lib):
     assert L.diffus_workspace_bytes(C.byref(vd), C.byref(fd), C.byref(pd), 1) > 0
     bad = B.VolumeDesc(1, 16, 16, 0, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0)
     assert L.diffus_workspace_bytes(C.byref(bad), C.byref(fd), C.byref(pd), 0) == 0
+    long_axis = B.VolumeDesc(4, 4, 70000, 0, 1.0, 1.0, 1.0, 0.0, 0.0, 0.0)   # an axis beyond 65535 voxels
+    assert L.diffus_workspace_bytes(C.byref(long_axis), C.byref(fd), C.byref(pd), 1) == 0
     # host-side rejection before any device work
     vp = C.c_void_p
     rc = L.diffus_render_fwd(None, C.byref(vd), vp(16), C.byref(fd), C.byref(pd), vp(16), None, None, vp(256),
