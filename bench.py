@@ -132,12 +132,12 @@ N_EVENTS = 10
 # adjoints; the gather adds the 8 corner weights and, per cell, the pose
 # terms that the sampled gradient and the pose chain rule give).
 ALGO_BYTES = {"march_fwd": 4.0, "blur": 8.0, "blur_T": 8.0, "march_bwd": 8.0, "gather_units": 4.0}
-ALGO_OPS = {"march_fwd": 111.0, "march_bwd": 99.0, "gather_units": 45.0}
+ALGO_OPS = {"march_fwd": 111.0, "march_bwd": 97.0, "gather_units": 45.0}
 BOUND = {"march_fwd": "alu", "march_bwd": "alu", "gather_units": "alu", "blur": "hbm", "blur_T": "hbm"}
 # DRAM bytes per ray-sample measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch over the 64-pose prefix of the
 # workload, divided by its ray-samples); absent where the kernel changed since.
-NCU_DRAM_PER_UNIT = {"march_fwd": 6.31, "blur": 6.03, "blur_T": 6.03}
+NCU_DRAM_PER_UNIT = {"march_fwd": 6.31, "blur": 6.12, "blur_T": 6.13, "march_bwd": 11.80, "gather_units": 7.19}
 
 
 def median_pose_order(fans):
