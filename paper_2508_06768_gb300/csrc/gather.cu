@@ -17,7 +17,8 @@ constexpr int kScanChunk = 4096;
 __global__ void k_ray_runs(const RayGeo *__restrict__ geo, const long long *__restrict__ gz_off, int n_rays,
                            GatherArgs G, int cap, uint32_t sentinel,
                            Run *__restrict__ runs, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                           int *__restrict__ nrun, uint32_t *__restrict__ status)
+                           int *__restrict__ nrun, unsigned long long *__restrict__ brick_work,
+                           uint32_t *__restrict__ status)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rays) return;
@@ -54,6 +55,7 @@ __global__ void k_ray_runs(const RayGeo *__restrict__ geo, const long long *__re
             runs[slot] = run;
             keys[slot] = brick;
             vals[slot] = (uint32_t)slot;
+            atomicAdd(brick_work + brick, (unsigned long long)run.len);   // for the unit order only
             cnt++;
         } else if (status) {
             atomicOr(status + 2, (uint32_t)DIFFUS_STATUS_QUEUE);
@@ -248,6 +250,53 @@ __global__ void k_unit_bricks(const uint32_t *__restrict__ ustart, const uint32_
     for (uint32_t i = 0; i < c; i++) unit_brick[u0 + i] = (uint32_t)b;
 }
 
+// Work class of each unit, one thread per unit: its share of its brick's
+// samples (a unit of m of the brick's n runs gets m/n of them), binned as
+// class = 31 - floor(log2(samples)), largest first; with a histogram of
+// the classes.
+__global__ void k_unit_work(const unsigned long long *__restrict__ brick_work, const uint32_t *__restrict__ bstart,
+                            const uint32_t *__restrict__ bend, const uint32_t *__restrict__ ustart,
+                            const uint32_t *__restrict__ unit_brick, const uint32_t *__restrict__ n_units,
+                            uint32_t *__restrict__ uclass, uint32_t *__restrict__ class_count)
+{
+    const uint32_t total = *n_units;
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x) {
+        const int b = (int)unit_brick[u];
+        const uint32_t n = bend[b] - bstart[b];
+        const uint32_t r0 = (u - ustart[b]) * kUnitRuns;
+        const uint32_t m = min((uint32_t)kUnitRuns, n - r0);
+        const unsigned long long w = brick_work[b] * m / n;
+        const uint32_t c = (uint32_t)__clzll(w | 1ull) - 32u;   // 31 - floor(log2(w)) for w < 2^32
+        const uint32_t cc = c > 31u ? 0u : c;                    // w >= 2^32 (not reached): largest class
+        uclass[u] = cc;
+        atomicAdd(class_count + cc, 1u);   // integer counts: order-free
+    }
+}
+
+// Exclusive scan of the 32 class counts into cursors (one warp).
+__global__ void k_class_cursors(uint32_t *__restrict__ class_count)
+{
+    const int lane = threadIdx.x;
+    const uint32_t c = class_count[lane];
+    uint32_t x = c;
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    class_count[lane] = x - c;
+}
+
+// The units in order of their work class, largest first.  The order inside
+// a class is whatever the atomics give: it decides only which warp takes a
+// unit when, never a result (every unit writes its own partial).
+__global__ void k_unit_order(const uint32_t *__restrict__ uclass, const uint32_t *__restrict__ n_units,
+                             uint32_t *__restrict__ cursor, uint32_t *__restrict__ order)
+{
+    const uint32_t total = *n_units;
+    for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < total; u += gridDim.x * blockDim.x)
+        order[atomicAdd(cursor + uclass[u], 1u)] = u;
+}
+
 // One warp per unit, units handed out by a ticket queue: the warp gathers
 // the unit's runs into its own 9^3 accumulator and writes the unit's
 // partial (with POSE, also each run's pose-gradient sums).  Warps are
@@ -258,7 +307,8 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
                    const uint32_t *__restrict__ bstart, const uint32_t *__restrict__ bend,
                    const uint32_t *__restrict__ ustart, const uint32_t *__restrict__ unit_brick,
                    const uint32_t *__restrict__ n_units, GatherArgs G, float *__restrict__ upart,
-                   uint32_t *__restrict__ queue, const T *__restrict__ vol, PoseOut po)
+                   uint32_t *__restrict__ queue, const uint32_t *__restrict__ order, const T *__restrict__ vol,
+                   PoseOut po)
 {
     __shared__ GatherSmem<POSE> sm;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -269,6 +319,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
         if (lane == 0) u = atomicAdd(queue, 1u);
         u = __shfl_sync(0xffffffffu, u, 0);
         if (u >= total) break;
+        u = order[u];   // longest-first
         const int b = (int)unit_brick[u];
         const uint32_t part = u - ustart[b];
         const uint32_t r0 = bstart[b] + part * kUnitRuns;
@@ -439,6 +490,8 @@ struct GatherLayout {
     uint32_t *keys[2], *vals[2];
     uint32_t *hist, *sums, *misc;   // misc: [0] units total, [1] scan total, [2] unit queue
     uint32_t *bstart, *bend, *ucount, *ustart, *unit_brick;
+    uint32_t *uclass, *uorder, *classes;   // unit work classes, the longest-first order, 32 class counters
+    unsigned long long *bwork;             // samples of each brick's runs
     float *upart;
     float *rpart;   // per-run pose-gradient sums, 6 x slots
     int *nrun;      // runs of each ray
@@ -469,6 +522,10 @@ static GatherLayout gather_layout(void *ws, const diffus_volume_desc *vd, long l
     L.ucount = c.take<uint32_t>(nb);
     L.ustart = c.take<uint32_t>(nb);
     L.unit_brick = c.take<uint32_t>(max_units);
+    L.uclass = c.take<uint32_t>(max_units);
+    L.uorder = c.take<uint32_t>(max_units);
+    L.classes = c.take<uint32_t>(32);
+    L.bwork = c.take<unsigned long long>(nb);
     L.upart = c.take<float>(max_units * kBrickVox);
     L.rpart = c.take<float>(6 * slots);
     L.nrun = c.take<int>((size_t)n_rays);
@@ -495,7 +552,7 @@ static void launch_units(const float *gz, const GatherLayout &L, int cur, const 
 {
     k_gather_units<T, POSE><<<grid, kGatherWarps * 32, 0, s>>>(gz, L.runs, L.vals[cur], L.bstart, L.bend, L.ustart,
                                                              L.unit_brick, L.misc + 0, G, L.upart, L.misc + 2,
-                                                             (const T *)vol, po);
+                                                             L.uorder, (const T *)vol, po);
 }
 
 int launch_gather(const diffus_volume_desc *vd, const void *vol, const RayGeo *geo, long long n_rays,
@@ -513,8 +570,9 @@ int launch_gather(const diffus_volume_desc *vd, const void *vol, const RayGeo *g
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 
+    if (cudaMemsetAsync(L.bwork, 0, sizeof(unsigned long long) * nb, s) != cudaSuccess) return DIFFUS_E_LAUNCH;
     k_ray_runs<<<(unsigned)((n_rays + 127) / 128), 128, 0, s>>>(geo, gz_off, (int)n_rays, G, cap, sentinel, L.runs,
-                                                               L.keys[0], L.vals[0], L.nrun, status);
+                                                               L.keys[0], L.vals[0], L.nrun, L.bwork, status);
     // stable LSD radix sort by brick
     const int nblk = (int)((slots + kSortTile - 1) / kSortTile);
     int cur = 0;
@@ -531,6 +589,12 @@ int launch_gather(const diffus_volume_desc *vd, const void *vol, const RayGeo *g
     k_unit_counts<<<(nb + 255) / 256, 256, 0, s>>>(L.bstart, L.bend, nb, L.ucount);
     launch_scan(L.ucount, L.ustart, (size_t)nb, L.sums, L.misc + 0, s);
     k_unit_bricks<<<(nb + 255) / 256, 256, 0, s>>>(L.ustart, L.ucount, nb, L.unit_brick);
+    // longest-first unit order (by classes of work), so that no long unit starts last
+    if (cudaMemsetAsync(L.classes, 0, 32 * sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
+    k_unit_work<<<sms, 256, 0, s>>>(L.bwork, L.bstart, L.bend, L.ustart, L.unit_brick, L.misc + 0, L.uclass,
+                                    L.classes);
+    k_class_cursors<<<1, 32, 0, s>>>(L.classes);
+    k_unit_order<<<sms * 4, 256, 0, s>>>(L.uclass, L.misc + 0, L.classes, L.uorder);
     record_mark(marks.units, marks.external, s);
     if (cudaMemsetAsync(L.misc + 2, 0, sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
     const int grid = sms * ctas_per_sm;
