@@ -60,6 +60,16 @@ struct alignas(16) Run {
 };
 static_assert(sizeof(Run) == 64, "Run layout");
 
+// A 64-bit fixed-point quantity as a float, from two 32-bit conversions
+// (high word x 2^32 + low word): within about an ulp.  The direct 64-bit
+// integer conversion runs on the FP64 pipe, which is narrow on this part;
+// every use here is an estimate that exact integer tests correct, or the
+// weight slope of a cell record.
+__device__ __forceinline__ float ll_to_float(long long x)
+{
+    return fmaf((float)(int)(x >> 32), 4294967296.0f, (float)(unsigned)(x & 0xffffffffll));
+}
+
 // First k in [0, kmax+1] with X0 + k DX >= L for DX > 0, or kmax+1 if no
 // k <= kmax qualifies.  Exact in fixed point: the float estimate is off by
 // at most a step or two and is corrected with integer tests.
@@ -67,9 +77,9 @@ __device__ __forceinline__ long long first_at_or_above(long long X0, long long D
 {
     if (X0 >= L) return 0;
     if (X0 + (kmax + 1) * DX < L) return kmax + 1;
-    float est = ceilf((float)(L - X0) / (float)DX);
-    long long k = est < 0.0f ? 0 : (long long)est;
-    if (k > kmax + 1) k = kmax + 1;
+    float est = ceilf(__fdividef(ll_to_float(L - X0), ll_to_float(DX)));
+    est = fminf(fmaxf(est, 0.0f), (float)(int)(kmax + 1));   // kmax < 2^31: 32-bit conversions
+    long long k = (long long)(int)est;
     while (k > 0 && X0 + (k - 1) * DX >= L) k--;
     while (k <= kmax && X0 + k * DX < L) k++;
     return k;
@@ -154,8 +164,8 @@ constexpr int kGCellCap = 32;  // samples of one cell record at most (bounds the
 __device__ __forceinline__ int ceil_div_fixed(long long num, long long den, int cap)
 {
     // smallest k >= 1 with k den >= num (num >= 1, den >= 1), at most cap
-    float est = ceilf((float)num / (float)den);
-    long long k = est < 1.0f ? 1 : (est > (float)cap ? cap : (long long)est);
+    float est = ceilf(__fdividef(ll_to_float(num), ll_to_float(den)));
+    long long k = est < 1.0f ? 1 : (est > (float)cap ? cap : (long long)(int)est);
     while (k > 1 && (k - 1) * den >= num) k--;
     while (k < cap && k * den < num) k++;
     return (int)k;
@@ -177,7 +187,8 @@ __device__ __forceinline__ void axis_cell(long long X, long long dX, int n, int 
     } else {
         i = (int)(X >> 32);
         u = __uint_as_float(0x3F800000u | ((unsigned)X >> 9)) - 1.0f;   // 23-bit fraction
-        v = (float)dX * 2.3283064365386963e-10f;                        // dX / 2^32
+        v = fmaf((float)(unsigned)(dX & 0xffffffffll), 2.3283064365386963e-10f,
+                 (float)(int)(dX >> 32));                               // dX / 2^32
     }
 }
 
