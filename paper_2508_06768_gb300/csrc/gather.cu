@@ -349,25 +349,27 @@ __global__ void __launch_bounds__(kGatherWarps * 32)
 }
 
 // The bricks whose cells touch voxel v along one axis, with v's index
-// inside each brick's 9 voxels: the brick of cell v-1 when v is on its far
-// face (or v is the last voxel), then the brick of cell v.  At most two.
-__device__ __forceinline__ int voxel_bricks(int v, int n, int (&b)[2], int (&l)[2])
+// inside each brick's 9 voxels: first the brick of cell v-1 when v is on its
+// far face (or v is the last voxel), then the brick of cell v.  Returns how
+// many (1 or 2); the entries are (b0, l0) and (b1, l1), scalars so that
+// they stay in registers.
+struct AxisBricks {
+    int n, b0, l0, b1, l1;
+};
+
+__device__ __forceinline__ AxisBricks voxel_bricks(int v, int n)
 {
-    int k = 0;
-    if (v >= 1) {
-        const int c = (v - 1) >> 3;
-        if (!(v <= n - 2 && c == (v >> 3))) {
-            b[k] = c;
-            l[k] = v - c * kBrick;
-            k++;
-        }
-    }
-    if (v <= n - 2) {
-        b[k] = v >> 3;
-        l[k] = v - (v >> 3) * kBrick;
-        k++;
-    }
-    return k;
+    const int own = v >> 3;                  // brick of cell v (when v <= n-2)
+    const int low = (v - 1) >> 3;            // brick of cell v-1 (when v >= 1)
+    const bool has_own = v <= n - 2;
+    const bool has_low = v >= 1 && !(has_own && low == own);
+    AxisBricks a;
+    a.n = (int)has_low + (int)has_own;
+    a.b0 = has_low ? low : own;
+    a.l0 = v - a.b0 * kBrick;
+    a.b1 = own;
+    a.l1 = v - own * kBrick;
+    return a;
 }
 
 // Each voxel: sum over the bricks whose cells touch it (z outer, then y,
@@ -379,19 +381,29 @@ __global__ void k_voxel_reduce(const float *__restrict__ upart, const uint32_t *
     const int vx = blockIdx.x * blockDim.x + threadIdx.x;
     const int vy = blockIdx.y, vz = blockIdx.z;
     if (vx >= G.nx) return;
-    int bx[2], lx[2], by[2], ly[2], bz[2], lz[2];
-    const int kx = voxel_bricks(vx, G.nx, bx, lx);
-    const int ky = voxel_bricks(vy, G.ny, by, ly);
-    const int kz = voxel_bricks(vz, G.nz, bz, lz);
+    const AxisBricks ax = voxel_bricks(vx, G.nx), ay = voxel_bricks(vy, G.ny), az = voxel_bricks(vz, G.nz);
     float s = 0.0f;
-    for (int iz = 0; iz < kz; iz++)
-        for (int iy = 0; iy < ky; iy++)
-            for (int ix = 0; ix < kx; ix++) {
-                const int b = (bz[iz] * G.nby + by[iy]) * G.nbx + bx[ix];
-                const int li = (lz[iz] * kBrickV + ly[iy]) * kBrickV + lx[ix];
+    // fixed trip counts with guards: every index is static
+#pragma unroll
+    for (int iz = 0; iz < 2; iz++) {
+        if (iz >= az.n) break;
+        const int bz = iz ? az.b1 : az.b0, lz = iz ? az.l1 : az.l0;
+#pragma unroll
+        for (int iy = 0; iy < 2; iy++) {
+            if (iy >= ay.n) break;
+            const int by = iy ? ay.b1 : ay.b0, ly = iy ? ay.l1 : ay.l0;
+#pragma unroll
+            for (int ix = 0; ix < 2; ix++) {
+                if (ix >= ax.n) break;
+                const int bx = ix ? ax.b1 : ax.b0, lx = ix ? ax.l1 : ax.l0;
+                const int b = (bz * G.nby + by) * G.nbx + bx;
+                const int li = (lz * kBrickV + ly) * kBrickV + lx;
                 const uint32_t u0 = ustart[b], u1 = u0 + ucount[b];
-                for (uint32_t u = u0; u < u1; u++) s += upart[(size_t)u * kBrickVox + li];
+                const float *p = upart + (size_t)u0 * kBrickVox + li;
+                for (uint32_t u = u0; u < u1; u++, p += kBrickVox) s += *p;
             }
+        }
+    }
     grad_vol[((size_t)vz * G.ny + vy) * G.nx + vx] = s;
 }
 
