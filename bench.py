@@ -137,7 +137,7 @@ BOUND = {"march_fwd": "alu", "march_bwd": "alu", "gather_units": "alu", "blur": 
 # DRAM bytes per ray-sample measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch over the 64-pose prefix of the
 # workload, divided by its ray-samples); absent where the kernel changed since.
-NCU_DRAM_PER_UNIT = {"march_fwd": 6.31, "blur": 6.12, "blur_T": 6.13, "march_bwd": 11.80, "gather_units": 7.19}
+NCU_DRAM_PER_UNIT = {"march_fwd": 6.31, "blur": 6.12, "blur_T": 6.13, "march_bwd": 11.80, "gather_units": 7.44}
 
 
 def median_pose_order(fans):
@@ -612,11 +612,16 @@ def run_native(args):
         cpu, err = cpu_leg(vol, poses, fans, prm, images=images_h, grad_poses=gposes_h,
                            G=G.cpu().numpy(), offsets=r.offsets)
 
-    # kernels per step: ray setup, forward march, [blur], [blur transpose],
-    # adjoint march, pose reduction; gather: brick runs, 2 radix passes of
+    # kernels per step: pose frames, ray setup, forward march, [blur, blur
+    # transpose] or [two depth-gain row passes], adjoint march, pose
+    # reduction; gather: brick runs, one radix pass per 8 bits of brick id of
     # (histogram, 3 scan kernels, scatter), brick bounds, unit counts, 3 scan
-    # kernels, unit-brick table, unit gather, voxel reduction
-    launches = 4 + (2 if prm.blur else 0) + (1 + 2 * 5 + 1 + 1 + 3 + 1 + 1 + 1)
+    # kernels, unit-brick table, unit work, class cursors, unit order, unit
+    # gather, voxel reduction, per-ray pose terms (memsets are not kernels)
+    nbricks = int(np.prod([(n - 2) // 8 + 1 for n in vol.data.shape]))
+    passes = (nbricks.bit_length() + 7) // 8
+    launches = (5 + (2 if prm.blur else (2 if prm.atten else 0)) +
+                (1 + 5 * passes + 1 + 1 + 3 + 1 + 3 + 1 + 1 + 1))
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
