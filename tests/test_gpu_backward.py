@@ -87,6 +87,18 @@ def _case(name):
         fan = I.Fan(19, 300 + 7, math.radians(75), 70.0, 6.0, 0.7)
         pose = np.array([12.0, 30.0, -3.0, 0.2, -0.4, 0.7], dtype=np.float32)
         return vol, pose, fan, I.Params(seed=5, mode=1, gshift=1)
+    if name == "grid_exact":
+        # every coordinate on the fixed-point grid: the middle ray of the odd
+        # fan runs along x = 0 exactly (dX = 0), and its z coordinate is
+        # -2 + k/4 mm, exactly 0 at sample 8; the other rays start clamped at
+        # x < 0.  Where a coordinate is exactly 0 the sampled impedance's
+        # derivative along that axis is taken as 0 on every side.
+        rng = np.random.default_rng(12)
+        vol = I.Volume((1.5 + 0.1 * rng.random((12, 12, 12))).astype(np.float32), (1.0, 1.0, 1.0),
+                       (0.0, 0.0, 0.0))
+        fan = I.Fan(5, 40, 0.8, 10.0, 5.0, 0.5)
+        pose = np.array([0.0, 3.0, -2.125, 0.0, 0.0, 0.0], dtype=np.float32)
+        return vol, pose, fan, I.Params(mode=1, seed=9)
     rng = np.random.default_rng(4)
     vol = I.Volume((1.5 + 0.2 * rng.random((3, 4, 5))).astype(np.float32), (1.0, 0.8, 1.3), (0.2, -0.1, 0.3))
     fan = I.Fan(5, 61, 0.9, 6.0, 5.0, 0.5)
@@ -94,13 +106,14 @@ def _case(name):
     return vol, pose, fan, I.Params(mode=1, seed=3)
 
 
-@pytest.mark.parametrize("name", ["small", "clamped", "tiny"])
+@pytest.mark.parametrize("name", ["small", "clamped", "tiny", "grid_exact"])
 def test_pose_gradient_with_and_without_volume_gradient(name):
     # With a volume gradient the brick gather forms the pose terms from the
     # cells' corners; without one the adjoint march samples dZ/dp itself.
     # Both against the oracle, and against each other.
     vol, pose, fan, prm = _case(name)
-    G = _loss_weights(vol, pose, fan, prm, seed=13) if name != "tiny" else I.random_weights((5, 61), 9)
+    G = (_loss_weights(vol, pose, fan, prm, seed=13) if name not in ("tiny", "grid_exact")
+         else I.random_weights((fan.n_rays, fan.n_samples), 9))
     _, rpose = oracle.render_grad(vol, pose, fan, prm, G.astype(np.float64))
     _, gp_full = gpu_grad(vol, pose, fan, prm, G)
     gv, gp_only = gpu_grad(vol, pose, fan, prm, G, want_vol=False)
