@@ -155,8 +155,10 @@ int diffus_render_fwd(const void *vol, const diffus_volume_desc *vd, const float
  * grad_vol (device float32, same dims as the volume, overwritten, nullable)
  * and grad_pose (device float[6], overwritten, nullable).  The forward is
  * recomputed per ray; nothing is kept from the forward call.  The volume
- * gradient is gathered per brick without floating-point atomics, so both
- * outputs are bitwise reproducible.  Workspace of
+ * gradient is gathered per brick without floating-point atomics; with it,
+ * the same brick walk also forms the pose gradient, while a call with
+ * grad_vol == NULL forms the pose gradient in the adjoint march and runs no
+ * gather.  Both outputs are bitwise reproducible.  Workspace of
  * diffus_workspace_bytes(..., 1) bytes. */
 int diffus_render_bwd(const void *vol, const diffus_volume_desc *vd, const float *pose,
                       const diffus_fan *fan, const diffus_params *prm, const float *grad_image,

@@ -103,7 +103,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
 
     for (int s = nseg - 1; s >= 0; s--) {
         const int base = s * kSeg;
-        // A': samples base .. base+255 with gradients; sample base+256 carried
+        // A': samples base .. base+255 (with dZ/dp when POSE); sample base+256 carried
         long long X, Y, Z;
         sample_pos(rg, base + lane, X, Y, Z);
         const long long sX = rg.DX[0] * kWarp, sY = rg.DX[1] * kWarp, sZ = rg.DX[2] * kWarp;
