@@ -556,9 +556,23 @@ def run_native(args):
             if it > 0:
                 tt += e0.elapsed_time(e1)
         e2e_ms = tt / n_e2e
+        # the link itself: one pinned 256 MiB copy each way, alone on the GPU
+        probe_h = torch.empty(64 << 20, dtype=torch.float32).pin_memory()
+        probe_d = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+        link = {}
+        for name, dst, src in (("h2d_gbs", probe_d, probe_h), ("d2h_gbs", probe_h, probe_d)):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            link[name] = probe_h.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        del probe_h, probe_d
         e2e = {"value": total * ws / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
-               "form": "one diffus_render_batch call per step; uploads and downloads overlap the marches"}
+               "form": "one diffus_render_batch call per step; uploads and downloads overlap the marches",
+               "link": link}
     clk.__exit__(None, None, None)
     clocks = clk.summary()
 
