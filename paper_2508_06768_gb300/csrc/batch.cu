@@ -112,6 +112,7 @@ struct BatchLayout {
     unsigned *counter;
     float *gy;       // blur transpose of grad_images (blur on)
     float *mbuf;     // speckle factors of every row, kept by the forward for the adjoint (speckle on)
+    float2 *kbuf;    // (impedance, r of the interface before) of every sample, kept by the forward for the adjoint
     float *gz;
     double *part;
     float4 *ckpt;
@@ -131,6 +132,7 @@ BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc
     L.fwd_bytes = c.used;
     L.gy = (blur || atten) ? c.take<float>((size_t)H.total_img) : nullptr;
     L.mbuf = speckle ? c.take<float>((size_t)H.total_img) : nullptr;
+    L.kbuf = c.take<float2>((size_t)H.total_gz);
     L.gz = c.take<float>((size_t)H.total_gz);
     L.part = c.take<double>(6 * (size_t)H.total_rays);
     L.ckpt = c.take<float4>((size_t)H.total_ckpt);
@@ -140,6 +142,13 @@ BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc
 }
 
 // ------------------------------------------------------------------ kernels
+
+// What the forward keeps for the adjoint of the same call (each nullable).
+struct FwdKeep {
+    float4 *ckpt;
+    float *mbuf;
+    float2 *kbuf;
+};
 
 struct BatchDev {
     const PlanPose *pose;
@@ -166,7 +175,7 @@ __global__ void __launch_bounds__(WARPS * 32, REFINE ? 1 : kFwdThreadsPerSM / (W
                                                           const RayGeo *__restrict__ geo, float *__restrict__ out,
                                                           int *__restrict__ valid, uint32_t *__restrict__ status,
                                                           unsigned *__restrict__ counter, float4 *__restrict__ ckpt,
-                                                          float *__restrict__ mbuf)
+                                                          float *__restrict__ mbuf, float2 *__restrict__ kbuf)
 {
     __shared__ float buf[WARPS][kSegPad];
     __shared__ double dbuf[REFINE ? WARPS : 1][REFINE ? kSegPad : 1];
@@ -184,7 +193,7 @@ __global__ void __launch_bounds__(WARPS * 32, REFINE ? 1 : kFwdThreadsPerSM / (W
             Ap.a2d = B.pose[rg.pose].a2d;
         }
         RayOut o{out + B.row_off[r], valid ? valid + r : nullptr, status, ckpt ? ckpt + B.ck_off[r] : nullptr,
-                 mbuf ? mbuf + B.row_off[r] : nullptr};
+                 mbuf ? mbuf + B.row_off[r] : nullptr, kbuf ? kbuf + B.gz_off[r] : nullptr};
         march_fwd_ray<T, REFINE>(vol, Ap, rg, o, buf[w], REFINE ? dbuf[w] : nullptr);
         __syncwarp();
     }
@@ -196,7 +205,8 @@ __global__ void __launch_bounds__(WARPS * 32, (POSE ? kBwdThreadsPerSM : kBwdVal
                                                           const float *__restrict__ gy, float *__restrict__ gz,
                                                           double *__restrict__ part, float4 *__restrict__ ckpt,
                                                           unsigned *__restrict__ counter,
-                                                          const float *__restrict__ mbuf)
+                                                          const float *__restrict__ mbuf,
+                                                          const float2 *__restrict__ kbuf)
 {
     __shared__ BwdSmem<POSE> sm[WARPS];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -212,8 +222,10 @@ __global__ void __launch_bounds__(WARPS * 32, (POSE ? kBwdThreadsPerSM : kBwdVal
             Ap.a2 = B.pose[rg.pose].a2;
             Ap.a2d = B.pose[rg.pose].a2d;
         }
-        march_bwd_ray<T, POSE>(vol, Ap, rg, gy + B.row_off[r], gz + B.gz_off[r], part + 6 * (size_t)r,
-                         ckpt + B.ck_off[r], sm[w], true, mbuf ? mbuf + B.row_off[r] : nullptr);
+        // the value-only march reads the samples the forward kept
+        march_bwd_ray<T, POSE, !POSE>(vol, Ap, rg, gy + B.row_off[r], gz + B.gz_off[r], part + 6 * (size_t)r,
+                                      ckpt + B.ck_off[r], sm[w], true, mbuf ? mbuf + B.row_off[r] : nullptr,
+                                      kbuf + B.gz_off[r]);
         __syncwarp();
     }
 }
@@ -280,39 +292,38 @@ int sm_count()
 
 template <typename T, int WARPS>
 void launch_fwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out, int *valid,
-                  uint32_t *status, unsigned *counter, float4 *ckpt, float *mbuf, int grid, bool refine,
-                  cudaStream_t s)
+                  uint32_t *status, unsigned *counter, const FwdKeep &kp, int grid, bool refine, cudaStream_t s)
 {
     if (refine)
         k_batch_fwd<T, WARPS, true><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status,
-                                                                counter, ckpt, mbuf);
+                                                                counter, kp.ckpt, kp.mbuf, kp.kbuf);
     else
         k_batch_fwd<T, WARPS, false><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status,
-                                                                 counter, ckpt, mbuf);
+                                                                 counter, kp.ckpt, kp.mbuf, kp.kbuf);
 }
 
 template <typename T, int WARPS>
 void launch_bwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, const float *gy,
-                  float *gz, double *part, float4 *ckpt, unsigned *counter, const float *mbuf, int grid, bool pose,
-                  cudaStream_t s)
+                  float *gz, double *part, float4 *ckpt, unsigned *counter, const float *mbuf, const float2 *kbuf,
+                  int grid, bool pose, cudaStream_t s)
 {
     if (pose)
         k_batch_bwd<T, WARPS, true><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, gy, gz, part, ckpt,
-                                                                counter, mbuf);
+                                                                counter, mbuf, kbuf);
     else
         k_batch_bwd<T, WARPS, false><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, gy, gz, part, ckpt,
-                                                                 counter, mbuf);
+                                                                 counter, mbuf, kbuf);
 }
 
 template <typename T>
 int launch_fwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out,
-                 int *valid, uint32_t *status, unsigned *counter, float4 *ckpt, float *mbuf, int grid, bool refine,
+                 int *valid, uint32_t *status, unsigned *counter, const FwdKeep &kp, int grid, bool refine,
                  cudaStream_t s)
 {
     switch (warps) {
-    case 2: launch_fwd_t<T, 2>(vol, A, B, geo, out, valid, status, counter, ckpt, mbuf, grid, refine, s); break;
-    case 4: launch_fwd_t<T, 4>(vol, A, B, geo, out, valid, status, counter, ckpt, mbuf, grid, refine, s); break;
-    case 8: launch_fwd_t<T, 8>(vol, A, B, geo, out, valid, status, counter, ckpt, mbuf, grid, refine, s); break;
+    case 2: launch_fwd_t<T, 2>(vol, A, B, geo, out, valid, status, counter, kp, grid, refine, s); break;
+    case 4: launch_fwd_t<T, 4>(vol, A, B, geo, out, valid, status, counter, kp, grid, refine, s); break;
+    case 8: launch_fwd_t<T, 8>(vol, A, B, geo, out, valid, status, counter, kp, grid, refine, s); break;
     default: return DIFFUS_E_PLAN;
     }
     return DIFFUS_OK;
@@ -320,13 +331,13 @@ int launch_fwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev 
 
 template <typename T>
 int launch_bwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, const float *gy,
-                 float *gz, double *part, float4 *ckpt, unsigned *counter, const float *mbuf, int grid, bool pose,
-                 cudaStream_t s)
+                 float *gz, double *part, float4 *ckpt, unsigned *counter, const float *mbuf, const float2 *kbuf,
+                 int grid, bool pose, cudaStream_t s)
 {
     switch (warps) {
-    case 2: launch_bwd_t<T, 2>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, grid, pose, s); break;
-    case 4: launch_bwd_t<T, 4>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, grid, pose, s); break;
-    case 8: launch_bwd_t<T, 8>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, grid, pose, s); break;
+    case 2: launch_bwd_t<T, 2>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, kbuf, grid, pose, s); break;
+    case 4: launch_bwd_t<T, 4>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, kbuf, grid, pose, s); break;
+    case 8: launch_bwd_t<T, 8>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, kbuf, grid, pose, s); break;
     default: return DIFFUS_E_PLAN;
     }
     return DIFFUS_OK;
@@ -525,15 +536,19 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     MarchArgs A = make_march_args(vd, &dummy, prm);
     const int grid = sm_count() * H.ctas_per_sm;
     float *march_out = prm->blur ? L.y : images;
-    // with a backward in the same call the forward keeps the scan carries
-    float4 *ck = bwd ? L.ckpt : nullptr;
-    float *mb = bwd ? L.mbuf : nullptr;
+    // with a backward in the same call the forward keeps the scan carries and
+    // speckle factors, and, for the value-only adjoint (volume gradient
+    // asked), every sample's impedance and every interface's coefficient
+    // (the adjoint samples dZ/dp itself only in a pose-only call)
+    const bool march_pose = grad_poses && !grad_vol;
+    const bool keep_samples = bwd && !march_pose;
+    const FwdKeep kp{bwd ? L.ckpt : nullptr, bwd ? L.mbuf : nullptr, keep_samples ? L.kbuf : nullptr};
     if (vd->dtype == DIFFUS_F32)
-        rc = launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0, ck, mb, grid,
+        rc = launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0, kp, grid,
                                  prm->refine != 0, s);
     else
         rc = launch_fwd_w<unsigned short>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0,
-                                          ck, mb, grid, prm->refine != 0, s);
+                                          kp, grid, prm->refine != 0, s);
     if (rc) return rc;
     const int rgrid = (int)std::min<int64_t>((H.total_rays + 7) / 8, (int64_t)sm_count() * 16);
     // the depth gain rides on the blur's output; without blur it is a row pass
@@ -565,14 +580,13 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     }
     mark(DIFFUS_TR_MARCH_BWD);
     // with a volume gradient the gather also forms the pose terms, so the
-    // adjoint march samples values only
-    const bool march_pose = grad_poses && !grad_vol;
+    // adjoint march reads the kept samples (march_pose above)
     if (vd->dtype == DIFFUS_F32)
-        rc = launch_bwd_w<float>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, L.mbuf, grid,
-                                 march_pose, s);
+        rc = launch_bwd_w<float>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, L.mbuf, L.kbuf,
+                                 grid, march_pose, s);
     else
         rc = launch_bwd_w<unsigned short>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, L.mbuf,
-                                          grid, march_pose, s);
+                                          L.kbuf, grid, march_pose, s);
     if (rc) return rc;
     mark(DIFFUS_TR_GATHER);
     if (grad_vol) {

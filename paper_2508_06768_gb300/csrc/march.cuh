@@ -36,6 +36,7 @@ struct RayOut {
     uint32_t *status; // nullable
     float4 *ckpt;     // nullable: scan carry (b0, b1, D) at every segment start, for the adjoint
     float *mrow;      // nullable: speckle factor of every row, for the adjoint
+    float2 *krow;     // nullable: per sample k = 0..S, (zref + dz, r_{k-1}) for the adjoint (r_{-1} = 0)
 };
 
 __device__ __forceinline__ int smem_idx(int x) { return x + (x >> 3); }
@@ -50,10 +51,11 @@ __device__ __forceinline__ void sample_pos(const RayGeo &rg, int k, long long &X
 // Phase A of a segment: samples base+1 .. base+256 lane-interleaved and
 // writes r_i (i = base..base+255, 0 past the ray) into buf[smem_idx(i-base)].
 // (czr, cdz) carries the sample at `base` in and the one at base+256 out.
+// krow (nullable) also receives, per sample k, (zref + dz, r_{k-1}).
 template <typename T, bool REFINE = false>
 __device__ __forceinline__ void seg_reflections(const T *__restrict__ vol, const VolGeo &g, const RayGeo &rg,
                                                 int base, float &czr, float &cdz, float *__restrict__ buf,
-                                                double *__restrict__ dbuf = nullptr)
+                                                double *__restrict__ dbuf = nullptr, float2 *__restrict__ krow = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int S = rg.S;
@@ -74,6 +76,7 @@ __device__ __forceinline__ void seg_reflections(const T *__restrict__ vol, const
         if (lane == 0) { lzr = pzr; ldz = pdz; }
         float r = (k - 1 < S) ? refl(lzr, ldz, zr, dz) : 0.0f;
         buf[smem_idx(t * kWarp + lane)] = r;
+        if (krow && k <= S) krow[k] = make_float2(zr + dz, r);
         if (REFINE) dbuf[smem_idx(t * kWarp + lane)] = (k - 1 < S) ? refl64(lzr, ldz, zr, dz) : 0.0;
         pzr = __shfl_sync(0xffffffffu, zr, 31);
         pdz = __shfl_sync(0xffffffffu, dz, 31);
@@ -241,6 +244,7 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
 
     float czr, cdz;
     sample_z<T, false>(vol, A.g, rg.X0[0], rg.X0[1], rg.X0[2], czr, cdz);
+    if (out.krow && lane == 0) out.krow[0] = make_float2(czr + cdz, 0.0f);
     float bs0 = 0.0f, bs1 = 1.0f, Ds = 1.0f;   // bottom row and det at segment start
     int first_bad = 0x7fffffff;
     int nonfinite = 0;
@@ -250,7 +254,7 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
 
     for (int base = 0; base < S; base += kSeg) {
         if (out.ckpt && lane == 0) out.ckpt[base / kSeg] = make_float4(bs0 + es0, bs1 + es1, Ds + esD, 0.0f);
-        seg_reflections<T, REFINE>(vol, A.g, rg, base, czr, cdz, buf, dbuf);
+        seg_reflections<T, REFINE>(vol, A.g, rg, base, czr, cdz, buf, dbuf, out.krow);
         __syncwarp();
         const int i0 = base + lane * kChunk;
         float rr[kChunk];

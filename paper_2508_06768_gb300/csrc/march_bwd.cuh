@@ -24,7 +24,7 @@ constexpr int kBwdPad = 289;   // smem_idx(256) + 1
 
 template <bool POSE>
 struct BwdSmem {
-    float zr[kBwdPad], dz[kBwdPad];   // samples base .. base+256 (zref + dz form)
+    float zr[kBwdPad], dz[kBwdPad];   // samples base .. base+256 (zref + dz form; STORED: zref + dz, r before)
     float gx[POSE ? kBwdPad : 1], gy[POSE ? kBwdPad : 1], gz[POSE ? kBwdPad : 1];   // dZ/dp (POSE)
     double acc[POSE ? 6 : 1];         // the ray's pose-gradient sums (lane 0)
 };
@@ -53,12 +53,17 @@ __device__ __forceinline__ EchoGrad echo_grad(float b0, float b1, float D, float
 // carries into ckpt, so the recording sweep is skipped.
 // mrow: speckle factors written by the forward of the same call (nullable;
 // recomputed from Philox when absent).
-template <typename T, bool POSE>
+// STORED (requires have_ckpt, not POSE): the forward of the same call kept,
+// per sample k, (zref + dz, r_{k-1}) in krow, so the march reads them instead
+// of resampling the volume (the same values bit for bit).
+template <typename T, bool POSE, bool STORED = false>
 __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, const RayGeo &rg,
                               const float *__restrict__ gy_row, float *__restrict__ gz_row,
                               double *__restrict__ pose_part, float4 *__restrict__ ckpt, BwdSmem<POSE> &sm,
-                              bool have_ckpt = false, const float *__restrict__ mrow = nullptr)
+                              bool have_ckpt = false, const float *__restrict__ mrow = nullptr,
+                              const float2 *__restrict__ krow = nullptr)
 {
+    static_assert(!(STORED && POSE), "the pose terms of the march need the sampled gradient");
     const int lane = threadIdx.x & 31;
     const int S = rg.S;
     const uint32_t pose = A.sp.pose_ctr + (uint32_t)rg.pose;
@@ -66,7 +71,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
     float *buf = sm.zr;   // sweep 1 uses the first array for reflection coefficients
 
     // ---------------- sweep 1: forward, record the carry at segment starts
-    if (!have_ckpt) {
+    if (!STORED && !have_ckpt) {
         float czr, cdz;
         sample_z<T, false>(vol, A.g, rg.X0[0], rg.X0[1], rg.X0[2], czr, cdz);
         float bs0 = 0.0f, bs1 = 1.0f, Ds = 1.0f;
@@ -113,10 +118,15 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
             int k = base + p;
             float zr = 0.0f, dz = 0.0f, g3[3] = {0.0f, 0.0f, 0.0f};
             if (k <= S) {
-                if (POSE)
+                if (STORED) {   // zr <- the sample's impedance, dz <- r of the interface before it
+                    const float2 kv = __ldg(krow + k);
+                    zr = kv.x;
+                    dz = kv.y;
+                } else if (POSE) {
                     sample_z<T, true>(vol, A.g, X, Y, Z, zr, dz, g3);
-                else
+                } else {
                     sample_z<T, false>(vol, A.g, X, Y, Z, zr, dz);
+                }
             }
             X += sX;
             Y += sY;
@@ -130,7 +140,11 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                 long long X, Y, Z;
                 float g3[3];
                 sample_pos(rg, base + kSeg, X, Y, Z);
-                if (POSE) {
+                if (STORED) {
+                    const float2 kv = __ldg(krow + base + kSeg);
+                    czr = kv.x;
+                    cdz = kv.y;
+                } else if (POSE) {
                     sample_z<T, true>(vol, A.g, X, Y, Z, czr, cdz, g3);
                     cg0 = g3[0]; cg1 = g3[1]; cg2 = g3[2];
                 } else {
@@ -154,7 +168,10 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
 #pragma unroll
         for (int t = 0; t < kChunk; t++) {
             int o = smem_idx(lane * kChunk + t), o1 = smem_idx(lane * kChunk + t + 1);
-            rr[t] = (i0 + t < S) ? refl(sm.zr[o], sm.dz[o], sm.zr[o1], sm.dz[o1]) : 0.0f;
+            if (STORED)   // r_{i0+t} is kept with sample i0+t+1
+                rr[t] = (i0 + t < S) ? sm.dz[o1] : 0.0f;
+            else
+                rr[t] = (i0 + t < S) ? refl(sm.zr[o], sm.dz[o], sm.zr[o1], sm.dz[o1]) : 0.0f;
         }
         Mat2 Q, E, Qall;
         float dq, de, dall;
@@ -291,7 +308,9 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                 le0 = n0;
                 le1 = n1;
                 const int o1 = smem_idx(lane * kChunk + t), o2 = smem_idx(lane * kChunk + t + 1);
-                const float z1 = sm.zr[o1] + sm.dz[o1], z2 = sm.zr[o2] + sm.dz[o2], sz = z1 + z2;
+                const float z1 = STORED ? sm.zr[o1] : sm.zr[o1] + sm.dz[o1];
+                const float z2 = STORED ? sm.zr[o2] : sm.zr[o2] + sm.dz[o2];
+                const float sz = z1 + z2;
                 const float is2 = frcp(sz * sz);
                 gzc = gr * (-2.0f * z2) * is2;
                 gzn = gr * (2.0f * z1) * is2;
