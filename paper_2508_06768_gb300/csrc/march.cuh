@@ -76,7 +76,7 @@ __device__ __forceinline__ void seg_reflections(const T *__restrict__ vol, const
         if (lane == 0) { lzr = pzr; ldz = pdz; }
         float r = (k - 1 < S) ? refl(lzr, ldz, zr, dz) : 0.0f;
         buf[smem_idx(t * kWarp + lane)] = r;
-        if (krow && k <= S) krow[k] = make_float2(zr + dz, r);
+        if (krow && k <= S) __stcs(krow + k, make_float2(zr + dz, r));
         if (REFINE) dbuf[smem_idx(t * kWarp + lane)] = (k - 1 < S) ? refl64(lzr, ldz, zr, dz) : 0.0;
         pzr = __shfl_sync(0xffffffffu, zr, 31);
         pdz = __shfl_sync(0xffffffffu, dz, 31);
@@ -284,7 +284,7 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
         if (out.mrow) {
 #pragma unroll
             for (int t = 0; t < kChunk; t++)
-                if (i0 + t < S) out.mrow[i0 + t] = m[t];
+                if (i0 + t < S) __stcs(out.mrow + i0 + t, m[t]);
         }
         float y[kChunk];
         if (!REFINE) {
