@@ -394,12 +394,12 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
         }
         if (vec4 && i0 + kChunk <= S) {
             float4 *dst = reinterpret_cast<float4 *>(out.row + i0);
-            dst[0] = make_float4(y[0], y[1], y[2], y[3]);
-            dst[1] = make_float4(y[4], y[5], y[6], y[7]);
+            __stcs(dst, make_float4(y[0], y[1], y[2], y[3]));
+            __stcs(dst + 1, make_float4(y[4], y[5], y[6], y[7]));
         } else {
 #pragma unroll
             for (int t = 0; t < kChunk; t++)
-                if (i0 + t < S) out.row[i0 + t] = y[t];
+                if (i0 + t < S) __stcs(out.row + i0 + t, y[t]);
         }
         __syncwarp();
     }

@@ -119,7 +119,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
             float zr = 0.0f, dz = 0.0f, g3[3] = {0.0f, 0.0f, 0.0f};
             if (k <= S) {
                 if (STORED) {   // zr <- the sample's impedance, dz <- r of the interface before it
-                    const float2 kv = __ldg(krow + k);
+                    const float2 kv = __ldcs(krow + k);
                     zr = kv.x;
                     dz = kv.y;
                 } else if (POSE) {
@@ -141,7 +141,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                 float g3[3];
                 sample_pos(rg, base + kSeg, X, Y, Z);
                 if (STORED) {
-                    const float2 kv = __ldg(krow + base + kSeg);
+                    const float2 kv = __ldcs(krow + base + kSeg);
                     czr = kv.x;
                     cdz = kv.y;
                 } else if (POSE) {
@@ -199,7 +199,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
         float m[kChunk];
         if (mrow) {
 #pragma unroll
-            for (int t = 0; t < kChunk; t++) m[t] = (i0 + t < S) ? __ldg(mrow + i0 + t) : 1.0f;
+            for (int t = 0; t < kChunk; t++) m[t] = (i0 + t < S) ? __ldcs(mrow + i0 + t) : 1.0f;
         } else if (A.sp.on) {
             chunk_speckle(A.sp, i0, S, rg.ray, pose, m);
         } else {
@@ -208,7 +208,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
         }
         float ge[kChunk];
 #pragma unroll
-        for (int t = 0; t < kChunk; t++) ge[t] = (i0 + t < S) ? m[t] * __ldg(gy_row + i0 + t) : 0.0f;
+        for (int t = 0; t < kChunk; t++) ge[t] = (i0 + t < S) ? m[t] * __ldcs(gy_row + i0 + t) : 0.0f;
 
         // C': local reverse pass with zero adjoint at the chunk end
         float c0 = 0.0f, c1 = 0.0f, dloc = 0.0f;
@@ -321,7 +321,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                 const int k = i0 + t + 1;
                 if (k <= S) {
                     const float G = c_next + gzn;
-                    gz_row[k] = G;
+                    __stcs(gz_row + k, G);
                     add_pose(k, smem_idx(lane * kChunk + t + 1), G);
                 }
             }
@@ -340,12 +340,12 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
             const int k = i0 + kChunk;
             if (k <= S) {
                 const float G = n_last + nextc;
-                gz_row[k] = G;
+                __stcs(gz_row + k, G);
                 add_pose(k, smem_idx(lane * kChunk + kChunk), G);
             }
         }
         if (s == 0 && lane == 0) {
-            gz_row[0] = c_first;
+            __stcs(gz_row, c_first);
             add_pose(0, smem_idx(0), c_first);
         }
         carry_gz1 = __shfl_sync(0xffffffffu, c_first, 0);
