@@ -128,16 +128,17 @@ N_EVENTS = 10
 # Algorithmic work per ray-sample of each kernel (derivation in the design
 # notes): HBM bytes that the method must move, and lane operations that it
 # must execute (trilinear sample, Eq. 1 coefficient, 2x2 step, echo,
-# Philox speckle; the adjoint adds the reverse scan and the Eq. 1 and echo
-# adjoints; the gather adds the 8 corner weights and, per cell, the pose
-# terms that the sampled gradient and the pose chain rule give).
+# Philox speckle; the adjoint reads the forward's samples, recomputes the
+# state and adds the reverse scan and the Eq. 1 and echo adjoints; the
+# gather adds the 8 corner weights and, per cell, the pose terms that the
+# sampled gradient and the pose chain rule give).
 ALGO_BYTES = {"march_fwd": 4.0, "blur": 8.0, "blur_T": 8.0, "march_bwd": 8.0, "gather_units": 4.0}
-ALGO_OPS = {"march_fwd": 111.0, "march_bwd": 97.0, "gather_units": 45.0}
+ALGO_OPS = {"march_fwd": 111.0, "march_bwd": 77.0, "gather_units": 45.0}
 BOUND = {"march_fwd": "alu", "march_bwd": "alu", "gather_units": "alu", "blur": "hbm", "blur_T": "hbm"}
 # DRAM bytes per ray-sample measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch over the 64-pose prefix of the
 # workload, divided by its ray-samples); absent where the kernel changed since.
-NCU_DRAM_PER_UNIT = {"march_fwd": 6.31, "blur": 6.12, "blur_T": 6.13, "march_bwd": 11.80, "gather_units": 7.44}
+NCU_DRAM_PER_UNIT = {"march_fwd": 14.26, "blur": 6.12, "blur_T": 6.13, "march_bwd": 18.70, "gather_units": 7.44}
 
 
 def median_pose_order(fans):
@@ -533,7 +534,7 @@ def run_native(args):
         tr.event[3] = ev_fwd_end.cuda_event      # DIFFUS_TR_FWD_END
         tr.wait_before_bwd = ev_g.cuda_event
         tt = 0.0
-        n_e2e = max(1, min(args.steps, 5))
+        n_e2e = max(1, min(args.steps, 10))
         for it in range(n_e2e + 1):
             flush.zero_()
             e0.record(stream)

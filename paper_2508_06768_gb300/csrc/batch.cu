@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(WARPS * 32, REFINE ? 1 : kFwdThreadsPerSM / (W
         }
         RayOut o{out + B.row_off[r], valid ? valid + r : nullptr, status, ckpt ? ckpt + B.ck_off[r] : nullptr,
                  mbuf ? mbuf + B.row_off[r] : nullptr, kbuf ? kbuf + B.gz_off[r] : nullptr};
-        march_fwd_ray<T, REFINE>(vol, Ap, rg, o, buf[w], REFINE ? dbuf[w] : nullptr);
+        march_fwd_ray<T, REFINE, true>(vol, Ap, rg, o, buf[w], REFINE ? dbuf[w] : nullptr);
         __syncwarp();
     }
 }

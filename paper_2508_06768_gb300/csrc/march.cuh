@@ -225,7 +225,8 @@ __device__ __forceinline__ void chunk_speckle(const Speckle &sp, int i0, int S, 
 }
 
 // Forward march of one ray by one warp.  buf: this warp's shared row of
-// kSegPad floats; dbuf: kSegPad doubles when REFINE.
+// kSegPad floats; dbuf: kSegPad doubles when REFINE.  STREAM writes the
+// output row with evict-first stores (the batched kernel).
 //
 // REFINE adds one iterative-refinement pass of the depth recurrence
 // b_{i+1} = b_i M_i, D_{i+1} = D_i delta_i per segment: the FP32 states are
@@ -234,7 +235,7 @@ __device__ __forceinline__ void chunk_speckle(const Speckle &sp, int i0, int S, 
 // e_{i+1} = e_i M_i + rho_{i+1} (e_0 = 0) of e_i = b*_i - b_i (b* the states
 // of the FP64 coefficients) is solved in FP32 with the same scan (affine
 // maps), and the echoes use the corrected states b_i + e_i.
-template <typename T, bool REFINE = false>
+template <typename T, bool REFINE = false, bool STREAM = false>
 __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, const RayGeo &rg,
                               const RayOut &out, float *__restrict__ buf, double *__restrict__ dbuf = nullptr)
 {
@@ -393,13 +394,25 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
             }
         }
         if (vec4 && i0 + kChunk <= S) {
+            // STREAM (the batched kernel: gigabytes of one-pass rows):
+            // evict-first; ordinary stores for small single-pose rows
             float4 *dst = reinterpret_cast<float4 *>(out.row + i0);
-            __stcs(dst, make_float4(y[0], y[1], y[2], y[3]));
-            __stcs(dst + 1, make_float4(y[4], y[5], y[6], y[7]));
+            if (STREAM) {
+                __stcs(dst, make_float4(y[0], y[1], y[2], y[3]));
+                __stcs(dst + 1, make_float4(y[4], y[5], y[6], y[7]));
+            } else {
+                dst[0] = make_float4(y[0], y[1], y[2], y[3]);
+                dst[1] = make_float4(y[4], y[5], y[6], y[7]);
+            }
         } else {
 #pragma unroll
             for (int t = 0; t < kChunk; t++)
-                if (i0 + t < S) __stcs(out.row + i0 + t, y[t]);
+                if (i0 + t < S) {
+                    if (STREAM)
+                        __stcs(out.row + i0 + t, y[t]);
+                    else
+                        out.row[i0 + t] = y[t];
+                }
         }
         __syncwarp();
     }

@@ -64,6 +64,16 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                               const float2 *__restrict__ krow = nullptr)
 {
     static_assert(!(STORED && POSE), "the pose terms of the march need the sampled gradient");
+    // The batched call (STORED) streams gigabytes of one-pass rows: evict-
+    // first loads and stores keep them from displacing reused L2 lines.  The
+    // small single-pose rows stay ordinary.
+    auto ld_once = [](const float *p) { return STORED ? __ldcs(p) : __ldg(p); };
+    auto st_once = [](float *p, float v) {
+        if (STORED)
+            __stcs(p, v);
+        else
+            *p = v;
+    };
     const int lane = threadIdx.x & 31;
     const int S = rg.S;
     const uint32_t pose = A.sp.pose_ctr + (uint32_t)rg.pose;
@@ -199,7 +209,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
         float m[kChunk];
         if (mrow) {
 #pragma unroll
-            for (int t = 0; t < kChunk; t++) m[t] = (i0 + t < S) ? __ldcs(mrow + i0 + t) : 1.0f;
+            for (int t = 0; t < kChunk; t++) m[t] = (i0 + t < S) ? ld_once(mrow + i0 + t) : 1.0f;
         } else if (A.sp.on) {
             chunk_speckle(A.sp, i0, S, rg.ray, pose, m);
         } else {
@@ -208,7 +218,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
         }
         float ge[kChunk];
 #pragma unroll
-        for (int t = 0; t < kChunk; t++) ge[t] = (i0 + t < S) ? m[t] * __ldcs(gy_row + i0 + t) : 0.0f;
+        for (int t = 0; t < kChunk; t++) ge[t] = (i0 + t < S) ? m[t] * ld_once(gy_row + i0 + t) : 0.0f;
 
         // C': local reverse pass with zero adjoint at the chunk end
         float c0 = 0.0f, c1 = 0.0f, dloc = 0.0f;
@@ -321,7 +331,7 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                 const int k = i0 + t + 1;
                 if (k <= S) {
                     const float G = c_next + gzn;
-                    __stcs(gz_row + k, G);
+                    st_once(gz_row + k, G);
                     add_pose(k, smem_idx(lane * kChunk + t + 1), G);
                 }
             }
@@ -340,12 +350,12 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
             const int k = i0 + kChunk;
             if (k <= S) {
                 const float G = n_last + nextc;
-                __stcs(gz_row + k, G);
+                st_once(gz_row + k, G);
                 add_pose(k, smem_idx(lane * kChunk + kChunk), G);
             }
         }
         if (s == 0 && lane == 0) {
-            __stcs(gz_row, c_first);
+            st_once(gz_row, c_first);
             add_pose(0, smem_idx(0), c_first);
         }
         carry_gz1 = __shfl_sync(0xffffffffu, c_first, 0);
