@@ -254,8 +254,12 @@ int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan *fans, int3
  * nullable); grad_poses (device float [P][6], overwritten, nullable);
  * ray_valid (device int32, one per ray in pose order, nullable).  The plan
  * must come from diffus_batch_plan with the same blur parameters
- * (DIFFUS_E_PLAN otherwise).  Only kernels and async memsets are issued, so
- * the call can be captured in a CUDA graph and replayed. */
+ * (DIFFUS_E_PLAN otherwise).  With a backward, the forward keeps in the
+ * workspace what the adjoint of the same call needs (scan carries, speckle
+ * factors and, unless only grad_poses is asked, every sample's impedance
+ * and coefficient), so the adjoint does not resample the volume.  Only
+ * kernels and async memsets are issued, so the call can be captured in a
+ * CUDA graph and replayed. */
 int diffus_render_batch(const void *vol, const diffus_volume_desc *vd, const float *poses,
                         const void *plan_host, const void *plan_dev, const diffus_params *prm,
                         float *images, int32_t *ray_valid, const float *grad_images, float *grad_vol,
