@@ -89,6 +89,28 @@ def test_pose_only_batch_call():
         assert np.linalg.norm(a - b) <= 2 * GRAD_TOL * np.linalg.norm(b), (p, a, b)
 
 
+def test_backward_without_gradient_outputs():
+    # dL/dimage given but neither gradient asked: the forward keeps its
+    # samples for an adjoint whose results go nowhere; the call succeeds and
+    # its images equal those of a forward-only call
+    import torch
+    from paper_2508_06768_gb300 import binding as B
+    vol, poses, fans, prm = _workload(seed=29, count=4)
+    r = _renderer(vol, fans, prm)
+    pd = torch.from_numpy(poses).cuda()
+    r.run(pd)
+    torch.cuda.synchronize()
+    fwd_only = r.images.clone()
+    G = torch.from_numpy(np.concatenate([I.random_weights((f.n_rays, f.n_samples), 700 + p).ravel()
+                                         for p, f in enumerate(fans)])).cuda()
+    B.render_batch(r.volume, r.spacing, r.origin, pd, r.plan_host, r.plan_dev, r.params, r.images, r.workspace,
+                   ray_valid=r.ray_valid, grad_images=G, grad_vol=None, grad_poses=None, status=r.status)
+    torch.cuda.synchronize()
+    st = r.status.cpu().numpy().view(np.uint32)
+    assert st[1] == 0 and st[2] == 0, st
+    assert torch.equal(r.images, fwd_only)
+
+
 def test_batch_vs_oracle():
     import torch
     vol, poses, fans, prm = _workload(mode=0)
