@@ -71,3 +71,19 @@ def test_workspace_sizing_and_validation(lib):
                              vp(256), 1 << 20, None)
     assert rc == -5  # misaligned float volume
     assert L.diffus_strerror(-6).decode().startswith("workspace")
+
+
+def test_batch_workspace_covers_the_adjoint_state(lib):
+    # host-only planning: the forward+backward workspace holds, beyond the
+    # forward's, per sample the kept (impedance, r) pair and dL/dZ, and per
+    # echo row the blur-transposed dL/dy and the speckle factor
+    import math
+    import torch
+    from paper_2508_06768_gb300 import inputs as I
+    vol = torch.zeros((20, 18, 16), dtype=torch.float32)
+    fans = [I.Fan(7, 100, math.radians(50), 10.0, 5.0, 0.5), I.Fan(12, 333, math.radians(40), 33.3, 5.0, 0.5)]
+    _, offs, wsf, wsb = B.batch_plan(vol, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0), fans, I.Params(seed=1, mode=1))
+    rows = sum(f.n_rays * f.n_samples for f in fans)
+    samples = sum(f.n_rays * (f.n_samples + 1) for f in fans)
+    assert int(offs[-1]) == rows
+    assert wsb - wsf >= (8 + 4) * samples + (4 + 4) * rows
