@@ -14,7 +14,7 @@
  * pivoting, or a dense one for tiny rays), and d_0 is read from the solution.
  * No prefix product, scan or closed form is used here.
  *
- * Readings where the paper is silent (each also listed in the design notes):
+ * Readings where the paper is silent:
  *  - Section 2.3 (Eq. 3/4) indexing: a ray carries S+1 impedance samples
  *    Z_0..Z_S; interface i lies between samples i and i+1; depth k truncates
  *    after interface k-1 (unknowns g_0,d_0,...,g_k,d_k; d_k = 0).

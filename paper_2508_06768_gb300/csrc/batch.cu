@@ -16,9 +16,6 @@
 
 using namespace dfs;
 
-namespace dfs {
-}  // namespace dfs
-
 namespace {
 
 constexpr uint32_t kPlanMagic = 0x44465350u;   // "DFSP"
