@@ -12,19 +12,29 @@ from __future__ import annotations
 import numpy as np
 
 
-def shard_poses(work, world: int):
-    """Deterministic split of poses over `world` ranks, balanced by work
-    (ray-samples per pose): longest-processing-time-first greedy, ties by
-    pose index.  Returns one sorted index list per rank."""
+def shard_ranges(work, world: int):
+    """Contiguous split of poses 0..P-1 over `world` ranks, balanced by work
+    (ray-samples per pose): rank r owns [start_r, end_r), the cut placed where
+    the running work sum is closest to r/world of the total.  Contiguous
+    ranges keep each pose's global index as its speckle counter (a rank's
+    batch is built with pose counter start_r), so every rank renders exactly
+    the images of the unsharded batch.  Returns a list of (start, end)."""
     work = np.asarray(work, dtype=np.int64)
-    order = np.lexsort((np.arange(work.size), -work))
-    load = np.zeros(world, dtype=np.int64)
-    owned = [[] for _ in range(world)]
-    for p in order:
-        r = int(np.lexsort((np.arange(world), load))[0])   # least loaded, lowest rank on ties
-        owned[r].append(int(p))
-        load[r] += work[p]
-    return [sorted(o) for o in owned]
+    P = work.size
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    csum = np.concatenate([[0], np.cumsum(work)])
+    total = int(csum[-1])
+    cuts = [0]
+    for r in range(1, world):
+        target = total * r / world
+        i = int(np.searchsorted(csum, target))
+        # the boundary nearest the target, never before the previous cut
+        if i > 0 and (i > P or abs(csum[i - 1] - target) <= abs(csum[i] - target)):
+            i -= 1
+        cuts.append(min(max(i, cuts[-1]), P))
+    cuts.append(P)
+    return [(cuts[r], cuts[r + 1]) for r in range(world)]
 
 
 def allreduce_volume_grad(grad_vol, group=None):

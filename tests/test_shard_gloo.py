@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2508_06768_gb300 import inputs as I
-from paper_2508_06768_gb300.shard import shard_poses
+from paper_2508_06768_gb300.shard import shard_ranges
 
 
 def _case():
@@ -33,7 +33,8 @@ def _worker(rank, world, port, out):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     vol, poses, fans, prm = _case()
-    mine = shard_poses([f.n_rays * f.n_samples for f in fans], world)[rank]
+    start, end = shard_ranges([f.n_rays * f.n_samples for f in fans], world)[rank]
+    mine = range(start, end)
     g = np.zeros(vol.data.shape)
     gp = {}
     for p in mine:
@@ -56,15 +57,20 @@ def _free_port():
     return port
 
 
-def test_shard_poses_balanced_and_complete():
+def test_shard_ranges_contiguous_balanced_and_complete():
     work = [5, 9, 1, 7, 7, 3, 2, 8]
-    sh = shard_poses(work, 3)
-    flat = sorted(p for s in sh for p in s)
-    assert flat == list(range(len(work)))
-    loads = [sum(work[p] for p in s) for s in sh]
-    assert max(loads) - min(loads) <= max(work)
-    assert shard_poses(work, 3) == sh            # deterministic
-    assert shard_poses(work, 1) == [list(range(len(work)))]
+    sh = shard_ranges(work, 3)
+    assert sh[0][0] == 0 and sh[-1][1] == len(work)
+    assert all(a[1] == b[0] for a, b in zip(sh, sh[1:]))          # contiguous, no gaps
+    loads = [sum(work[a:b]) for a, b in sh]
+    assert max(loads) - min(loads) <= 2 * max(work)
+    assert shard_ranges(work, 3) == sh                            # deterministic
+    assert shard_ranges(work, 1) == [(0, len(work))]
+    assert sum(b - a for a, b in shard_ranges([4], 3)) == 1      # more ranks than poses
+    # the 512-pose batch over 8 ranks: every rank within 3 % of the mean
+    w = np.array([f.n_rays * f.n_samples for f in I.random_batch_fans(512, seed=4)])
+    loads = np.array([w[a:b].sum() for a, b in shard_ranges(w, 8)])
+    assert loads.sum() == w.sum() and loads.max() <= 1.03 * loads.mean()
 
 
 def test_two_rank_gradient_exchange_matches_single_process():
