@@ -112,9 +112,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def build_workload(rank=0, count=512, n=256):
+def build_workload(rank=0, count=512, n=256, replicas=False):
+    """The batch workload.  Replicas: rank r > 0 draws its own pose set.
+    Otherwise every rank builds the same job (it renders only its shard)."""
     vol, poses, fans, prm = I.workload_batch(count=512, n=n)
-    if rank:
+    if rank and replicas:
         poses = I.hemisphere_poses(vol, 512, seed=4 + 1000 * rank)
     return vol, poses[:count], fans[:count], prm
 
@@ -125,10 +127,9 @@ TRACE = {"ray_setup": (0, 1), "march_fwd": (1, 2), "blur": (2, 3), "blur_T": (3,
          "gather_sort": (5, 8), "gather_units": (8, 9), "voxel_reduce": (9, 6), "pose_reduce": (6, 7)}
 N_EVENTS = 10
 
-# Algorithmic work per ray-sample of each kernel (derivation in the design
-# notes): HBM bytes that the method must move, and lane operations that it
-# must execute (trilinear sample, Eq. 1 coefficient, 2x2 step, echo,
-# Philox speckle; the adjoint reads the forward's samples, recomputes the
+# Algorithmic work per ray-sample of each kernel: HBM bytes that the method
+# must move, and lane operations that it must execute (trilinear sample,
+# Eq. 1 coefficient, 2x2 step, echo, Philox speckle; the adjoint reads the forward's samples, recomputes the
 # state and adds the reverse scan and the Eq. 1 and echo adjoints; the
 # gather adds the 8 corner weights and, per cell, the pose terms that the
 # sampled gradient and the pose chain rule give).
@@ -138,7 +139,7 @@ BOUND = {"march_fwd": "alu", "march_bwd": "alu", "gather_units": "alu", "blur": 
 # DRAM bytes per ray-sample measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch over the 64-pose prefix of the
 # workload, divided by its ray-samples); absent where the kernel changed since.
-NCU_DRAM_PER_UNIT = {"march_fwd": 14.26, "blur": 6.12, "blur_T": 6.13, "march_bwd": 18.70, "gather_units": 7.44}
+NCU_DRAM_PER_UNIT = {"blur": 6.12, "blur_T": 6.13, "gather_units": 7.44}
 
 
 def median_pose_order(fans):
@@ -177,7 +178,7 @@ def cpu_leg(vol, poses, fans, prm, budget_s=10.0, max_poses=8, images=None, grad
             gimg = images[int(offsets[p]):int(offsets[p + 1])].reshape(f.n_rays, f.n_samples)
             md = np.minimum(det[:, :-1], det[:, 1:])
             ok = np.arange(f.n_samples)[None, :] < np.minimum(first - 1, f.n_samples)[:, None]
-            ok &= md >= 0.05
+            ok &= md >= IMG_MIN_DET
             if W:
                 # a blurred row mixes rays j-W..j+W: all of them must qualify
                 okw = ok.copy()
@@ -274,15 +275,17 @@ def _capture(torch, fn):
     return g
 
 
-def run_forms(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, stream, steps, warmup, total):
+def run_forms(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, stream, steps, warmup, total,
+              with_cpu=True):
     """The batched form against the plain single-pose kernel, and the other
     forms: forward only, speckle-off forward, BF16 volume."""
     from dataclasses import replace
     from paper_2508_06768_gb300.render import BatchRenderer
     out = {}
     dev = vol_d.device
-    # batched forward only
-    rf = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm, schedule=sched, with_bwd=False)
+    # batched forward only, in the forward-only call's default form (one
+    # lane per ray); the autotuned schedule is the forward+backward step's
+    rf = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm, with_bwd=False)
     g = _capture(torch, lambda s: rf.run(poses_d, None, stream=s))
     ms = _time_graph(torch, g, flush, stream, steps, warmup)
     out["batched_fwd"] = {"value": total / (ms * 1e-3), "ms": ms}
@@ -290,7 +293,7 @@ def run_forms(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, stream,
     del g, rf
     # batched forward, speckle and blur off (the form closest to bandwidth-bound)
     prm0 = replace(prm, speckle=0, blur=0)
-    rf = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm0, schedule=sched, with_bwd=False)
+    rf = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm0, with_bwd=False)
     g = _capture(torch, lambda s: rf.run(poses_d, None, stream=s))
     ms = _time_graph(torch, g, flush, stream, steps, warmup)
     out["batched_fwd_no_speckle_no_blur"] = {"value": total / (ms * 1e-3), "ms": ms}
@@ -335,7 +338,8 @@ def run_forms(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, stream,
     del g
     out["speedup_fwd_vs_plain"] = out["plain_fwd"]["ms"] / fwd_ms
     del img, gv, wsp
-    out.update(run_scale_form(torch, flush, stream, steps, warmup))
+    out.update(run_scale_form(torch, flush, stream, steps, warmup, with_err=with_cpu))
+    out.update(run_configs(torch, B, flush, stream, steps, warmup, with_cpu=with_cpu))
     out.update(run_next_rows(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, stream, steps, warmup, total))
     return out
 
@@ -410,7 +414,7 @@ def run_next_rows(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, str
     return out
 
 
-def run_scale_form(torch, flush, stream, steps, warmup):
+def run_scale_form(torch, flush, stream, steps, warmup, with_err=True):
     """Precision + scale workload: 512^3 BF16 volume at 0.5 mm, 64 hemisphere
     poses x 1024 rays x 4096 samples at 0.05 mm, 7 MHz, forward+backward,
     with and without the FP64-residual refinement pass."""
@@ -431,10 +435,196 @@ def run_scale_form(torch, flush, stream, steps, warmup):
         g = _capture(torch, lambda s: r5.run(poses5, G5, stream=s))
         ms = _time_graph(torch, g, flush, stream, max(1, min(steps, 5)), warmup)
         key = "scale_bf16_fwd_bwd_refine" if refine else "scale_bf16_fwd_bwd"
+        st = r5.status.cpu().numpy().view(np.uint32)
         out[key] = {"value": total5 / (ms * 1e-3), "ms": ms, "ray_samples": total5,
+                    "rays_with_pole": int(st[0]), "rays_refined": int(st[3]), "rays": 64 * 1024,
                     "workload": "512^3 BF16 at 0.5 mm, 64 poses x 1024 rays x 4096 samples at 0.05 mm, 7 MHz, "
                                 "literal |R|, speckle+blur%s" % (", FP64-residual refinement" if refine else "")}
+        if refine and with_err:
+            out[key]["err_vs_fp64"] = scale_errors(torch, v5, vb, poses5, fans5, prm5)
         del g, r5
+    if "scale_bf16_fwd_bwd" in out:
+        out["scale_refine_over_unrefined"] = out["scale_bf16_fwd_bwd_refine"]["ms"] / out["scale_bf16_fwd_bwd"]["ms"]
+    return out
+
+
+def scale_errors(torch, v5, vb, poses5, fans5, prm, n_sample=4, block=16):
+    """Error of the refined BF16-volume path against the FP64 oracle run on
+    the BF16-rounded volume: 4 seeded poses, a block of 16 central rays
+    each; images over every well-posed row, and the volume and pose
+    gradients of a loss that weights those blocks' rows with
+    min det >= 0.15."""
+    import oracle
+    from paper_2508_06768_gb300.render import BatchRenderer
+    q = I.Volume(torch.from_numpy(v5.data).to(torch.bfloat16).to(torch.float32).numpy(), v5.spacing, v5.origin)
+    N, S = fans5[0].n_rays, fans5[0].n_samples
+    rng = np.random.default_rng(5)
+    sampled = sorted(rng.choice(len(fans5), n_sample, replace=False).tolist())
+    j0 = (N - block) // 2
+    rays = np.arange(j0, j0 + block)
+    W = oracle.blur_halfwidth(prm)
+    refs, G = {}, np.zeros((len(fans5), N, S), np.float32)
+    for p in sampled:
+        ref, first, det = oracle.render(q, poses5[p].cpu().numpy(), fans5[p], prm, pose_ctr=p, rays=rays,
+                                        first_bad=True, dets=True)
+        ok = _rows_ok(first, det, S, W, 0.0)
+        refs[p] = (ref, ok)
+        G[p, rays] = np.where(_rows_ok(first, det, S, W, GRAD_MIN_DET), I.random_weights((block, S), 500 + p), 0.0)
+    r = BatchRenderer(vb, v5.spacing, v5.origin, fans5, prm, with_bwd=True)
+    r.run(poses5, torch.from_numpy(G.ravel()).cuda())
+    torch.cuda.synchronize()
+    num = den = 0.0
+    gp_num = gp_den = 0.0
+    gv_ref = np.zeros(v5.data.shape)
+    for p in sampled:
+        ref, ok = refs[p]
+        img = r.image(p).cpu().numpy()[rays].astype(np.float64)
+        num += float(np.sum((img - ref)[ok] ** 2))
+        den += float(np.sum(ref[ok] ** 2))
+        gv, gp = oracle.render_grad(q, poses5[p].cpu().numpy(), fans5[p], prm, G[p].astype(np.float64), pose_ctr=p)
+        gv_ref += gv
+        gp_num += float(np.sum((r.grad_poses[p].cpu().numpy() - gp) ** 2))
+        gp_den += float(np.sum(gp ** 2))
+    gvol = r.grad_vol.cpu().numpy()
+    return {"image_rel_l2": math.sqrt(num / den), "grad_pose_rel_l2": math.sqrt(gp_num / gp_den),
+            "grad_vol_rel_l2": float(np.linalg.norm(gvol - gv_ref) / np.linalg.norm(gv_ref)),
+            "poses": sampled, "rays": "%d..%d" % (rays[0], rays[-1]),
+            "rows": "images: every row before the first pole; gradients: rows with min det >= %g" % GRAD_MIN_DET,
+            "reference": "FP64 oracle on the BF16-rounded volume"}
+
+
+# Conditioning thresholds of the error statements, the parity tests' own:
+# images are held to the FP32 tolerance on rows whose min det is at least
+# 0.05 (every row with the refined pass); gradients are formed from rows
+# whose min det is at least 0.15, where the adjoint's 1/det^2 amplification
+# stays within the tolerance.
+IMG_MIN_DET = 0.05
+GRAD_MIN_DET = 0.15
+
+
+def _rows_ok(first, det, S, W, md_min):
+    """Rows before the first pole (over the blur window) with min(det A_k,
+    det A_k+1) >= md_min."""
+    md = np.minimum(det[:, :-1], det[:, 1:])
+    ok = np.arange(S)[None, :] < np.minimum(first - 1, S)[:, None]
+    ok &= md >= md_min
+    if W:
+        okw = ok.copy()
+        for d in range(1, W + 1):
+            okw[d:] &= ok[:-d]
+            okw[:-d] &= ok[d:]
+        ok = okw
+    return ok
+
+
+def run_configs(torch, B, flush, stream, steps, warmup, with_cpu=True):
+    """Configs 1-3 of the workload list, one pose each through the
+    single-pose entry points (graph replay): the plain forward on the 64^3
+    phantom, the plain forward of the 256x256x192 brain slice, and the
+    forward+backward of an MSE loss on the 64^3 phantom; each with its error
+    against the FP64 oracle and, on the host cores, the oracle's definition
+    route and the O(S) recurrence route."""
+    import oracle
+    from paper_2508_06768_gb300.render import render
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {}
+
+    def timed_fwd(vol, pose, fan, prm, reps):
+        v = torch.from_numpy(vol.data).to(dev)
+        pt = torch.from_numpy(np.asarray(pose, np.float32)).to(dev)
+        img, valid, st = B.render_fwd(v, vol.spacing, vol.origin, pt, fan, prm)
+        ws = B.alloc_workspace(B.workspace_bytes(B.volume_desc(v, vol.spacing, vol.origin), B.fan_desc(fan),
+                                                 B.params_desc(prm), False), dev)
+        g = _capture(torch, lambda s: B.render_fwd(v, vol.spacing, vol.origin, pt, fan, prm, image=img,
+                                                   ray_valid=valid, status=st, workspace=ws, stream=s))
+        ms = _time_graph(torch, g, flush, stream, reps, max(warmup, 10))
+        torch.cuda.synchronize()
+        return ms, img.cpu().numpy().astype(np.float64), valid.cpu().numpy()
+
+    def cpu_times(vol, pose, fan, prm, rays=None):
+        import cpu_baseline
+        t0 = time.perf_counter()
+        oracle.render(vol, pose, fan, prm, rays=rays)
+        t_def = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        cpu_baseline.render(vol, pose, fan, prm)
+        t_rec = time.perf_counter() - t0
+        nr = fan.n_rays if rays is None else len(rays)
+        return {"definition_route": nr * fan.n_samples / t_def, "recurrence_route": fan.n_rays * fan.n_samples / t_rec,
+                "cores": oracle.num_threads(), "unit": UNIT,
+                "definition_sample": "%d of %d rays" % (nr, fan.n_rays)}
+
+    # config 1: plain forward, 64^3 phantom, 64 rays x 256 samples
+    vol, pose, fan, prm = I.workload_small()
+    units = fan.n_rays * fan.n_samples
+    d = {"workload": "64^3 phantom at 1 mm, top-face pose, 64 rays x 256 samples to 60 mm, 5 MHz, literal |R|, "
+                     "speckle+blur, one diffus_render_fwd per graph replay"}
+    ref, first, det = oracle.render(vol, pose, fan, prm, first_bad=True, dets=True)
+    W = oracle.blur_halfwidth(prm)
+    for refine in (0, 1):
+        ms, img, valid = timed_fwd(vol, pose, fan, prm.with_(refine=refine), max(steps, 500))
+        ok_all = _rows_ok(first, det, fan.n_samples, W, 0.0)
+        ok_good = _rows_ok(first, det, fan.n_samples, W, IMG_MIN_DET)
+        e = {"ms": ms, "value": units / (ms * 1e-3),
+             "err_rows_min_det_0.05": float(np.linalg.norm((img - ref)[ok_good]) / np.linalg.norm(ref[ok_good])),
+             "err_all_well_posed_rows": float(np.linalg.norm((img - ref)[ok_all]) / np.linalg.norm(ref[ok_all])),
+             "ray_valid_matches": bool(np.array_equal(valid, np.minimum(first - 1, fan.n_samples)))}
+        d["refine" if refine else "fp32"] = e
+    if with_cpu:
+        d["cpu"] = cpu_times(vol, pose, fan, prm)
+    out["config1_plain_fwd"] = d
+
+    # config 2: plain forward of the brain slice, 256 rays x 1024 samples
+    vol2, pose2, fan2, prm2 = I.workload_brain_slice()
+    units2 = fan2.n_rays * fan2.n_samples
+    ms, img, valid = timed_fwd(vol2, pose2, fan2, prm2, max(steps, 50))
+    rays = np.arange(0, fan2.n_rays, 8)
+    ref2, first2, det2 = oracle.render(vol2, pose2, fan2, prm2, rays=rays, first_bad=True, dets=True)
+    ok2 = _rows_ok(first2, det2, fan2.n_samples, 0, IMG_MIN_DET)   # sampled rays: judged without their blur window
+    W2 = oracle.blur_halfwidth(prm2)
+    if W2:
+        # rows whose blur window meets a pole on any ray are left out
+        vmin = np.minimum(first2 - 1, fan2.n_samples)
+        ok2 &= np.arange(fan2.n_samples)[None, :] < vmin.min()
+    d = {"workload": "256x256x192 brain phantom at 1 mm, top-face pose, 256 rays x 1024 samples to 120 mm, 7 MHz, "
+                     "literal |R|, speckle+blur", "ms": ms, "value": units2 / (ms * 1e-3),
+         "err_vs_fp64": float(np.linalg.norm((img[rays] - ref2)[ok2]) / max(np.linalg.norm(ref2[ok2]), 1e-300)),
+         "err_rows": "every 8th ray, rows with min det >= 0.05 before the first pole of any sampled ray"}
+    if with_cpu:
+        d["cpu"] = cpu_times(vol2, pose2, fan2, prm2, rays=np.arange(0, fan2.n_rays, 32))
+    out["config2_brain_slice_fwd"] = d
+
+    # config 3: forward+backward of an MSE loss against a perturbed-pose render
+    v = torch.from_numpy(vol.data).to(dev)
+    target, _ = oracle.render(vol, I.perturbed_pose(pose, seed=3), fan, prm)
+    good = _rows_ok(first, det, fan.n_samples, W, GRAD_MIN_DET)
+    Gm = np.where(good, 2.0 * (ref - target) / ref.size, 0.0)
+    pt = torch.from_numpy(pose).to(dev)
+    img = torch.empty((fan.n_rays, fan.n_samples), device=dev)
+    gi = torch.from_numpy(Gm.astype(np.float32)).to(dev)
+    gv = torch.empty(vol.data.shape, device=dev)
+    gp = torch.empty(6, device=dev)
+    vd = B.volume_desc(v, vol.spacing, vol.origin)
+    ws = B.alloc_workspace(B.workspace_bytes(vd, B.fan_desc(fan), B.params_desc(prm), True), dev)
+
+    rv3 = torch.empty(fan.n_rays, dtype=torch.int32, device=dev)
+    st3 = torch.zeros(4, dtype=torch.int32, device=dev)
+
+    def step(s):
+        B.render_fwd(v, vol.spacing, vol.origin, pt, fan, prm, image=img, ray_valid=rv3, status=st3, workspace=ws,
+                     stream=s)
+        B.render_bwd(v, vol.spacing, vol.origin, pt, fan, prm, gi, grad_vol=gv, grad_pose=gp, status=st3,
+                     workspace=ws, stream=s)
+    g = _capture(torch, step)
+    ms = _time_graph(torch, g, flush, stream, max(steps, 200), max(warmup, 10))
+    rv, rp = oracle.render_grad(vol, pose, fan, prm, Gm)
+    out["config3_fwd_bwd"] = {
+        "workload": "64^3 phantom, 64 rays x 256 samples, MSE against a render at a +-3 mm / +-3 deg perturbed pose, "
+                    "gradients w.r.t. the FP32 volume and the 6-DoF pose",
+        "ms": ms, "value": units / (ms * 1e-3),
+        "grad_vol_rel_l2": float(np.linalg.norm(gv.cpu().numpy() - rv) / np.linalg.norm(rv)),
+        "grad_pose_rel_l2": float(np.linalg.norm(gp.cpu().numpy() - rp) / np.linalg.norm(rp)),
+        "rows": "dL/dimage on rows with min det >= %g before the first pole" % GRAD_MIN_DET}
     return out
 
 
@@ -444,26 +634,46 @@ def run_native(args):
     from paper_2508_06768_gb300 import binding as B
     from paper_2508_06768_gb300.render import BatchRenderer, autotune
 
+    from paper_2508_06768_gb300.shard import allreduce_volume_grad, shard_ranges
+
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=dev)
+    sharded = ws > 1 and not args.replicas
 
-    vol, poses, fans, prm = build_workload(rank, count=args.poses)
-    vol_d = torch.from_numpy(vol.data).to(dev)
-    poses_d = torch.from_numpy(poses).to(dev)
-    total = sum(f.n_rays * f.n_samples for f in fans)
+    vol, poses, fans, prm = build_workload(rank, count=args.poses, replicas=args.replicas)
+    job_total = sum(f.n_rays * f.n_samples for f in fans)
+    # dL/dimage of the whole job (seeded), so a shard's weights are the same
+    # slice of it whatever the rank count
     gen = torch.Generator(device=dev)
-    gen.manual_seed(1234 + rank)
-    G = torch.randn(total, generator=gen, device=dev, dtype=torch.float32)
+    gen.manual_seed(1234 + (rank if args.replicas else 0))
+    G_job = torch.randn(job_total, generator=gen, device=dev, dtype=torch.float32)
+    pose0 = 0
+    if sharded:
+        # one job split over the ranks: a contiguous, work-balanced pose range
+        # each (the pose counter of the speckle stays the global index); the
+        # volume gradients are summed over the ranks after every step
+        pose0, pose1 = shard_ranges([f.n_rays * f.n_samples for f in fans], ws)[rank]
+        offs_job = np.concatenate([[0], np.cumsum([f.n_rays * f.n_samples for f in fans])])
+        G_job = G_job[int(offs_job[pose0]):int(offs_job[pose1])]
+        poses, fans = poses[pose0:pose1], fans[pose0:pose1]
+    vol_d = torch.from_numpy(vol.data).to(dev)
+    poses_d = torch.from_numpy(np.ascontiguousarray(poses)).to(dev)
+    total = sum(f.n_rays * f.n_samples for f in fans)
+    G = G_job.contiguous()
 
     # project autotuner over the persistent schedule (small candidate set)
     sched = None
     if not args.no_autotune:
+        # (warps per CTA, CTAs per SM, gather CTAs per SM, forward form):
+        # form 0 runs the marches with one lane per ray (grids of 4-warp CTAs
+        # sized from warps x CTAs), form 1 with one warp per ray
         sched, _ = autotune(vol_d, vol.spacing, vol.origin, fans, prm, poses_d, G,
-                            candidates=[(8, 2, 8), (8, 3, 8), (8, 3, 16), (4, 6, 16), (2, 8, 8)], reps=1)
-    r = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm, schedule=sched, with_bwd=True)
+                            candidates=[(4, 3, 8, 0), (4, 4, 8, 0), (4, 4, 16, 0), (4, 6, 8, 0), (8, 3, 8, 1)],
+                            reps=1)
+    r = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm, schedule=sched, with_bwd=True, pose_ctr=pose0)
 
     events = [torch.cuda.Event(enable_timing=True) for _ in range(N_EVENTS)]
     for e in events:
@@ -476,11 +686,17 @@ def run_native(args):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    def exchange():
+        # the one exchange step of a sharded job: sum of the volume gradients
+        if sharded:
+            allreduce_volume_grad(r.grad_vol)
+
     # clocks are sampled from the warm-up to the end of the end-to-end leg
     clk = ClockSampler(local).__enter__()
     for _ in range(args.warmup):
         flush.zero_()
         graph.replay()
+        exchange()
     torch.cuda.synchronize()
     kern_ms = {k: 0.0 for k in TRACE}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -492,6 +708,7 @@ def run_native(args):
         flush.zero_()
         e0.record(stream)
         graph.replay()
+        exchange()
         e1.record(stream)
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
@@ -504,7 +721,9 @@ def run_native(args):
         total_ms = float(t.item())
         dist.barrier()
     ms_per_step = total_ms / args.steps
-    value = total * ws / (ms_per_step * 1e-3)
+    # whole job: every rank's units over the slowest rank's time
+    job_units = job_total if sharded else total * ws
+    value = job_units / (ms_per_step * 1e-3)
     kern_ms = {k: v / args.steps for k, v in kern_ms.items()}
     status = r.status.cpu().numpy().view(np.uint32)
     images_h = r.images.cpu().numpy()
@@ -548,6 +767,7 @@ def run_native(args):
             down.wait_event(ev_fwd_end)
             with torch.cuda.stream(down):
                 img_h.copy_(r.images, non_blocking=True)
+            exchange()
             gv_h.copy_(r.grad_vol, non_blocking=True)
             gp_h.copy_(r.grad_poses, non_blocking=True)
             stream.wait_stream(down)
@@ -557,6 +777,10 @@ def run_native(args):
             if it > 0:
                 tt += e0.elapsed_time(e1)
         e2e_ms = tt / n_e2e
+        if ws > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
         # the link itself: one pinned 256 MiB copy each way, alone on the GPU
         probe_h = torch.empty(64 << 20, dtype=torch.float32).pin_memory()
         probe_d = torch.empty(64 << 20, dtype=torch.float32, device=dev)
@@ -570,7 +794,7 @@ def run_native(args):
             torch.cuda.synchronize()
             link[name] = probe_h.numel() * 4 / (e0.elapsed_time(e1) * 1e-3) / 1e9
         del probe_h, probe_d
-        e2e = {"value": total * ws / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": job_units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
                "form": "one diffus_render_batch call per step; uploads and downloads overlap the marches",
                "link": link}
@@ -579,9 +803,9 @@ def run_native(args):
 
     # ---- forms: batched vs the plain single-pose kernel, forward only, speckle off, BF16
     forms = None
-    if not args.no_forms:
+    if not args.no_forms and ws == 1:
         forms = run_forms(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, stream, args.steps,
-                          args.warmup, total)
+                          args.warmup, total, with_cpu=not args.no_cpu)
         forms["batched_fwd_bwd"] = {"value": total / (ms_per_step * 1e-3), "ms": ms_per_step}
         forms["speedup_fwd_bwd_vs_plain"] = forms["plain_fwd_bwd"]["ms"] / ms_per_step
 
@@ -639,13 +863,19 @@ def run_native(args):
                 (1 + 5 * passes + 1 + 1 + 3 + 1 + 3 + 1 + 1 + 1))
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "strong" if sharded else "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD if len(fans) == 512 else "first %d poses of: %s" % (len(fans), WORKLOAD),
-                           "ray_samples_per_step_per_gpu": total, "poses": len(fans),
-                           "l2": "flushed between steps (2x129 MB write)", "parallelism": "replicas (weak)",
+                "config": {"workload": WORKLOAD if args.poses == 512 else "first %d poses of: %s" % (args.poses, WORKLOAD),
+                           "ray_samples_per_step_per_gpu": total, "ray_samples_per_step": job_units,
+                           "poses": len(fans) if not sharded else "%d of %d (rank 0 shard)" % (len(fans), args.poses),
+                           "l2": "flushed between steps (2x129 MB write)",
+                           "parallelism": ("replicas (weak): every rank renders its own 512-pose batch"
+                                           if args.replicas or ws == 1 else
+                                           "dp%d: one job, contiguous work-balanced pose shards, NCCL all-reduce "
+                                           "of the volume gradient every step" % ws),
                            "schedule": None if sched is None else [sched.rays_per_cta, sched.ctas_per_sm,
-                                                                   sched.brick]},
+                                                                   sched.brick, sched.fwd_form]},
                 "kernels": kernels,
                 "status": [int(x) for x in status],
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
@@ -667,6 +897,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--replicas", action="store_true",
+                    help="N>1: every rank renders its own batch (weak scaling) instead of a shard of one job")
     ap.add_argument("--poses", type=int, default=512,
                     help="poses of the batch (512 = the full workload; fewer only for profiler captures)")
     args = ap.parse_args()

@@ -35,7 +35,7 @@
  *      [0] rays that meet a pole of the depth system (see ray_valid),
  *      [1] non-finite image values written,
  *      [2] error bits (DIFFUS_STATUS_*),
- *      [3] reserved (0).
+ *      [3] rays redone by the refined pass (refine = 1; 0 otherwise).
  */
 #ifndef DIFFUS_H
 #define DIFFUS_H
@@ -106,11 +106,15 @@ typedef struct {
  *    exp(-m^2 / (2 s_k^2)), s_k = sigma0 + sigma1 (k+1)/S (in rays),
  *    W = ceil(3 (sigma0 + sigma1)) <= 32.
  *  refine: 1 adds one iterative-refinement pass to the forward solve of
- *    Eq. 2-4: the residuals of the FP32 depth recurrence are computed in
- *    FP64 (coefficients recomputed in FP64 from the same samples), the
- *    error recurrence is solved in FP32 and the echoes use the corrected
- *    states.  Any volume dtype, single-pose and batched forward; the
- *    adjoint stays FP32.
+ *    Eq. 2-4 on the rays that need it.  The FP32 pass lists a ray when an
+ *    echo row's conditioning min(det A_k, det A_k+1) falls below
+ *    max(0.05, 0.0025 sqrt(S)) (where its FP32 error may exceed 1e-5) or
+ *    the ray meets a pole.  The refined pass redoes such a ray up to its last such
+ *    row (at least to the pole, whose decision it takes again): residuals
+ *    of the FP32 depth recurrence are computed in FP64 against coefficients
+ *    from FP64 samples at the FP64 ray positions, the error recurrence is
+ *    solved in FP32 and the echoes use the corrected states.  Any volume
+ *    dtype, single-pose and batched forward; the adjoint stays FP32.
  *  atten (the two readings of "uniform attenuation", Section 2.1): 0 puts
  *    the amplitude factor a = 10^(-alpha f ds / 20) of every sample cell
  *    inside the rows of Eq. 4 (default); 1 solves the depth systems with
@@ -175,10 +179,19 @@ int diffus_render_bwd(const void *vol, const diffus_volume_desc *vd, const float
  * scratch is a fixed file-scope device array of DIFFUS_NOALLOC_SCRATCH_BYTES
  * (16 MiB) that every GPU loading the library holds until the process exits.
  * A request whose forward workspace (diffus_workspace_bytes(..., 0)) exceeds
- * it returns DIFFUS_E_SCRATCH before any launch; 16 MiB covers, for example,
- * 256 rays x 16384 samples or 2048 rays x 2048 samples with the blur on.
+ * it returns DIFFUS_E_SCRATCH before any launch.  That workspace is
+ * align256(112 n_rays) + 256 bytes, plus align256(4 n_rays n_samples) with the
+ * blur on and align256(8 n_rays) + align256(4 n_rays) + 256 with refine = 1
+ * (align256 rounds up to a multiple of 256), so with refine = 0 the limit
+ * admits, for example, 2048 rays x 2019 samples with the blur on (2048 x
+ * 2020 is rejected), 4096 x 995, or any fan of up to 149,000 rays with the
+ * blur off.
  * The first call on a device looks up the array's device address (once, with
- * that device current); make that first call before any stream capture.
+ * that device current) and keeps it for the life of the process; make that
+ * first call before any stream capture.  A cudaDeviceReset (or any other
+ * teardown of the device's primary context) leaves that address stale: after
+ * one, this entry point must not be used on that device again in the same
+ * process.
  * Every call shares the one array: calls whose work overlaps on the GPU
  * (other streams, other host threads) race on it and must be serialised by
  * the caller.  The paper has no counterpart: this is a deployment variant.
@@ -192,14 +205,19 @@ int diffus_render_fwd_noalloc(const void *vol, const diffus_volume_desc *vd, con
 /* Launch schedule of the batched path.  rays_per_cta: warps (one ray each)
  * per CTA of the persistent marches (2, 4 or 8); ctas_per_sm: resident CTAs
  * per SM used to size the persistent march grids; brick: CTAs per SM of the
- * volume-gradient gather grid (1..64).  Zero fields take defaults (4, 4, 8).
- * The schedule changes the launch shapes only, never the arithmetic of a
- * ray or a brick. */
+ * volume-gradient gather grid (1..64); fwd_form: how the forward march maps
+ * rays to lanes, 0 (default) one lane per ray over tiles of 32 consecutive
+ * rays of a pose (the rays' depth recurrences run side by side), 1 one warp
+ * per ray (lanes along the depth, combined by a warp scan).  Zero fields of
+ * the first three take defaults (4, 4, 8).  rays_per_cta, ctas_per_sm and
+ * brick change launch shapes only, never the arithmetic of a ray or a
+ * brick; the two forward forms order the FP32 arithmetic of a ray
+ * differently, so their images agree to rounding, not bitwise. */
 typedef struct {
     int32_t rays_per_cta;
     int32_t ctas_per_sm;
     int32_t brick;
-    int32_t reserved;
+    int32_t fwd_form;
 } diffus_schedule;
 
 /* Optional tracing of the batched call: when non-NULL, the library records

@@ -42,7 +42,7 @@ class ParamsDesc(C.Structure):
 
 class ScheduleDesc(C.Structure):
     _fields_ = [("rays_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32), ("brick", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("fwd_form", C.c_int32)]
 
 
 class ScanGridDesc(C.Structure):

@@ -13,6 +13,7 @@
 
 #include "host.hpp"
 #include "march_bwd.cuh"
+#include "march_bwd_tile.cuh"
 
 using namespace dfs;
 
@@ -38,12 +39,12 @@ struct BlurTile {                 // one 32-row strip of one pose image
 struct PlanHeader {
     uint32_t magic;
     int32_t P;
-    int64_t total_rays, total_img, total_gz, total_ckpt, n_tiles;
+    int64_t total_rays, total_img, total_gz, total_ckpt, n_tiles, n_ftiles, total_bcar;
     double max_depth;
     int32_t max_S, blurW;
-    int32_t warps, ctas_per_sm, gather_ctas, pad_;
+    int32_t warps, ctas_per_sm, gather_ctas, fwd_form;
     int64_t off_pose, off_depth, off_ray0, off_ray_pose, off_ray_j, off_order, off_row_off, off_gz_off, off_ck_off,
-        off_tiles;
+        off_tiles, off_ftiles;
     int64_t bytes;
     uint64_t params_fp;   // fingerprint of the parameters the plan was made for
 };
@@ -73,7 +74,7 @@ struct PlanSizes {
     int64_t bytes;
 };
 
-PlanSizes plan_sizes(int P, int64_t total_rays, int64_t n_tiles)
+PlanSizes plan_sizes(int P, int64_t total_rays, int64_t n_tiles, int64_t n_ftiles)
 {
     PlanSizes z;
     int64_t o = (int64_t)align256(sizeof(PlanHeader));
@@ -91,6 +92,7 @@ PlanSizes plan_sizes(int P, int64_t total_rays, int64_t n_tiles)
     put(7, sizeof(int64_t) * total_rays);
     put(8, sizeof(int64_t) * total_rays);
     put(9, sizeof(BlurTile) * n_tiles);
+    put(10, sizeof(TileDesc) * n_ftiles);
     z.bytes = o;
     return z;
 }
@@ -102,30 +104,49 @@ int64_t count_tiles(const diffus_fan *fans, int P)
     return t;
 }
 
+// Forward tiles: 32 consecutive rays of a pose per tile.
+int64_t count_ftiles(const diffus_fan *fans, int P)
+{
+    int64_t t = 0;
+    for (int p = 0; p < P; p++) t += (int64_t)((fans[p].n_rays + kWarp - 1) / kWarp);
+    return t;
+}
+
 struct BatchLayout {
     RayGeo *geo;
     PoseFrame *frames;
     float *y;        // pre-blur rows (blur on)
     unsigned *counter;
+    RefineSel sel;   // selective refinement (refine = 1)
     float *gy;       // blur transpose of grad_images (blur on)
     float *mbuf;     // speckle factors of every row, kept by the forward for the adjoint (speckle on)
     float2 *kbuf;    // (impedance, r of the interface before) of every sample, kept by the forward for the adjoint
     float *gz;
     double *part;
     float4 *ckpt;
+    float4 *bcar;    // 16-row carries of the lane-per-ray forward, for its backward
     void *gather_ws;
     size_t fwd_bytes, bytes;
 };
 
 BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc *vd, bool blur, bool speckle,
-                         bool atten)
+                         bool atten, bool refine)
 {
     Carve c(ws);
     BatchLayout L;
     L.geo = c.take<RayGeo>((size_t)H.total_rays);
     L.frames = c.take<PoseFrame>((size_t)H.P);
-    L.counter = c.take<unsigned>(4);
+    L.counter = c.take<unsigned>(8);
     L.y = blur ? c.take<float>((size_t)H.total_img) : nullptr;
+    L.sel = RefineSel{nullptr, nullptr, nullptr, nullptr};
+    if (refine) {
+        L.sel.rinfo = c.take<int2>((size_t)H.total_rays);
+        L.sel.rlist = c.take<int>((size_t)H.total_rays);
+        if (L.counter) {
+            L.sel.rcount = L.counter + 4;
+            L.sel.ticket = L.counter + 5;
+        }
+    }
     L.fwd_bytes = c.used;
     L.gy = (blur || atten) ? c.take<float>((size_t)H.total_img) : nullptr;
     L.mbuf = speckle ? c.take<float>((size_t)H.total_img) : nullptr;
@@ -133,6 +154,7 @@ BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc
     L.gz = c.take<float>((size_t)H.total_gz);
     L.part = c.take<double>(6 * (size_t)H.total_rays);
     L.ckpt = c.take<float4>((size_t)H.total_ckpt);
+    L.bcar = H.fwd_form == 0 ? c.take<float4>((size_t)H.total_bcar) : nullptr;
     L.gather_ws = (void *)c.take<char>(gather_workspace_bytes(vd, H.total_rays, H.max_depth));
     L.bytes = c.used;
     return L;
@@ -145,6 +167,7 @@ struct FwdKeep {
     float4 *ckpt;
     float *mbuf;
     float2 *kbuf;
+    float4 *bcar;
 };
 
 struct BatchDev {
@@ -167,15 +190,17 @@ __global__ void k_batch_setup(const PoseFrame *__restrict__ frames, BatchDev B, 
 }
 
 // Persistent forward: each warp takes rays from the queue (longest first).
-template <typename T, int WARPS, bool REFINE>
-__global__ void __launch_bounds__(WARPS * 32, REFINE ? 1 : kFwdThreadsPerSM / (WARPS * 32)) k_batch_fwd(const T *__restrict__ vol, MarchArgs A, BatchDev B,
+// With refinement on (sel.rinfo set) it is the FP32 pass, which lists the
+// rays that need the refined pass.
+template <typename T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, kFwdThreadsPerSM / (WARPS * 32)) k_batch_fwd(const T *__restrict__ vol, MarchArgs A, BatchDev B,
                                                           const RayGeo *__restrict__ geo, float *__restrict__ out,
                                                           int *__restrict__ valid, uint32_t *__restrict__ status,
                                                           unsigned *__restrict__ counter, float4 *__restrict__ ckpt,
-                                                          float *__restrict__ mbuf, float2 *__restrict__ kbuf)
+                                                          float *__restrict__ mbuf, float2 *__restrict__ kbuf,
+                                                          RefineSel sel)
 {
     __shared__ float buf[WARPS][kSegPad];
-    __shared__ double dbuf[REFINE ? WARPS : 1][REFINE ? kSegPad : 1];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
         unsigned q = 0;
@@ -190,8 +215,95 @@ __global__ void __launch_bounds__(WARPS * 32, REFINE ? 1 : kFwdThreadsPerSM / (W
             Ap.a2d = B.pose[rg.pose].a2d;
         }
         RayOut o{out + B.row_off[r], valid ? valid + r : nullptr, status, ckpt ? ckpt + B.ck_off[r] : nullptr,
-                 mbuf ? mbuf + B.row_off[r] : nullptr, kbuf ? kbuf + B.gz_off[r] : nullptr};
-        march_fwd_ray<T, REFINE, true>(vol, Ap, rg, o, buf[w], REFINE ? dbuf[w] : nullptr);
+                 mbuf ? mbuf + B.row_off[r] : nullptr, kbuf ? kbuf + B.gz_off[r] : nullptr,
+                 sel.rinfo ? sel.rinfo + r : nullptr, sel.rlist, sel.rcount, r};
+        march_fwd_ray<T, false, true>(vol, Ap, rg, o, buf[w]);
+        __syncwarp();
+    }
+}
+
+// Persistent forward with one lane per ray: each warp takes tiles of 32
+// consecutive rays of a pose from the queue (longest first).
+template <typename T>
+__global__ void __launch_bounds__(kTileWarps * 32, kFwdThreadsPerSM / (kTileWarps * 32)) k_batch_fwd_tiles(const T *__restrict__ vol, MarchArgs A, BatchDev B,
+                                                          const RayGeo *__restrict__ geo,
+                                                          const TileDesc *__restrict__ tiles, int64_t n_tiles,
+                                                          float *__restrict__ out, int *__restrict__ valid,
+                                                          uint32_t *__restrict__ status,
+                                                          unsigned *__restrict__ counter, float4 *__restrict__ ckpt,
+                                                          float *__restrict__ mbuf, float2 *__restrict__ kbuf,
+                                                          float4 *__restrict__ bcar, RefineSel sel)
+{
+    __shared__ TileSmem sm[kTileWarps];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned q = 0;
+        if (lane == 0) q = atomicAdd(counter, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if ((int64_t)q >= n_tiles) break;
+        const TileDesc tl = tiles[q];
+        MarchArgs Ap = A;
+        if (!A.atten) Ap.a2 = B.pose[tl.pose].a2;   // the depth-gain reading keeps a2 = 1
+        march_fwd_tile<T>(vol, Ap, tl, geo, out, valid, status, ckpt, mbuf, kbuf, bcar, sel, sm[w]);
+        __syncwarp();
+    }
+}
+
+// Persistent backward of the lane-per-ray forward (volume gradient asked):
+// tiles from the queue, longest first.
+__global__ void __launch_bounds__(kTileWarpsBwd * 32, kBwdValThreadsPerSM / (kTileWarpsBwd * 32)) k_batch_bwd_tiles(MarchArgs A, BatchDev B,
+                                                          const TileDesc *__restrict__ tiles, int64_t n_tiles,
+                                                          const float *__restrict__ gy, const float *__restrict__ mbuf,
+                                                          const float2 *__restrict__ kbuf,
+                                                          const float4 *__restrict__ bcar, float *__restrict__ gz,
+                                                          unsigned *__restrict__ counter)
+{
+    __shared__ BwdTileSmem sm[kTileWarpsBwd];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned q = 0;
+        if (lane == 0) q = atomicAdd(counter, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if ((int64_t)q >= n_tiles) break;
+        const TileDesc tl = tiles[q];
+        MarchArgs Ap = A;
+        if (!A.atten) Ap.a2 = B.pose[tl.pose].a2;
+        march_bwd_tile(Ap, tl, gy, mbuf, kbuf, bcar, gz, sm[w]);
+        __syncwarp();
+    }
+}
+
+// Refined pass of the batch over the rays the FP32 pass listed (in the order
+// it listed them, which follows its longest-first queue).
+template <typename T, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) k_batch_refine(const T *__restrict__ vol, MarchArgs A, BatchDev B,
+                                                                const RayGeo *__restrict__ geo,
+                                                                const PoseFrame *__restrict__ frames, VolPlace vp,
+                                                                float *__restrict__ out, int *__restrict__ valid,
+                                                                uint32_t *__restrict__ status,
+                                                                float4 *__restrict__ ckpt, RefineSel sel)
+{
+    __shared__ float buf[WARPS][kSegPad];
+    __shared__ double dbuf[WARPS][kSegPad];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned n = *sel.rcount;
+    for (;;) {
+        unsigned q = 0;
+        if (lane == 0) q = atomicAdd(sel.ticket, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= n) break;
+        const int r = sel.rlist[q];
+        const RayGeo rg = geo[r];
+        const PlanPose pp = B.pose[rg.pose];
+        MarchArgs Ap = A;
+        if (!A.atten) {
+            Ap.a2 = pp.a2;
+            Ap.a2d = pp.a2d;
+        }
+        const FanDev fd{pp.n_rays, pp.S, pp.fov, pp.depth};
+        RayOut o{out + B.row_off[r], valid ? valid + r : nullptr, status, ckpt ? ckpt + B.ck_off[r] : nullptr,
+                 nullptr, nullptr, nullptr, nullptr, nullptr, r};
+        refine_ray<T, true>(vol, Ap, rg, frames[rg.pose], fd, vp, o, sel.rinfo[r], buf[w], dbuf[w]);
         __syncwarp();
     }
 }
@@ -279,6 +391,7 @@ void launch_batch_blur(const float *in, float *out, const PlanPose *poses, const
     }
 }
 
+
 int sm_count()
 {
     int dev = 0, sms = 148;
@@ -287,16 +400,29 @@ int sm_count()
     return sms;
 }
 
+// The forward's launch: fwd_form 0 marches tiles with one lane per ray
+// (grid = CTAs per SM x SMs of kTileWarps warps), 1 one warp per ray.
+struct FwdLaunch {
+    int grid, form;
+    const TileDesc *tiles;
+    int64_t n_tiles;
+};
+
 template <typename T, int WARPS>
 void launch_fwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out, int *valid,
-                  uint32_t *status, unsigned *counter, const FwdKeep &kp, int grid, bool refine, cudaStream_t s)
+                  uint32_t *status, unsigned *counter, const FwdKeep &kp, const FwdLaunch &fl, const RefineSel &sel,
+                  const PoseFrame *frames, const VolPlace &vp, cudaStream_t s)
 {
-    if (refine)
-        k_batch_fwd<T, WARPS, true><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status,
-                                                                counter, kp.ckpt, kp.mbuf, kp.kbuf);
+    if (fl.form == 0)
+        k_batch_fwd_tiles<T><<<fl.grid, kTileWarps * 32, 0, s>>>((const T *)vol, A, B, geo, fl.tiles, fl.n_tiles,
+                                                                 out, valid, status, counter, kp.ckpt, kp.mbuf,
+                                                                 kp.kbuf, kp.bcar, sel);
     else
-        k_batch_fwd<T, WARPS, false><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status,
-                                                                 counter, kp.ckpt, kp.mbuf, kp.kbuf);
+        k_batch_fwd<T, WARPS><<<fl.grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status, counter,
+                                                             kp.ckpt, kp.mbuf, kp.kbuf, sel);
+    if (sel.rinfo)
+        k_batch_refine<T, WARPS><<<2 * sm_count(), WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, frames, vp, out, valid,
+                                                                  status, kp.ckpt, sel);
 }
 
 template <typename T, int WARPS>
@@ -314,13 +440,13 @@ void launch_bwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const 
 
 template <typename T>
 int launch_fwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out,
-                 int *valid, uint32_t *status, unsigned *counter, const FwdKeep &kp, int grid, bool refine,
-                 cudaStream_t s)
+                 int *valid, uint32_t *status, unsigned *counter, const FwdKeep &kp, const FwdLaunch &fl,
+                 const RefineSel &sel, const PoseFrame *frames, const VolPlace &vp, cudaStream_t s)
 {
     switch (warps) {
-    case 2: launch_fwd_t<T, 2>(vol, A, B, geo, out, valid, status, counter, kp, grid, refine, s); break;
-    case 4: launch_fwd_t<T, 4>(vol, A, B, geo, out, valid, status, counter, kp, grid, refine, s); break;
-    case 8: launch_fwd_t<T, 8>(vol, A, B, geo, out, valid, status, counter, kp, grid, refine, s); break;
+    case 2: launch_fwd_t<T, 2>(vol, A, B, geo, out, valid, status, counter, kp, fl, sel, frames, vp, s); break;
+    case 4: launch_fwd_t<T, 4>(vol, A, B, geo, out, valid, status, counter, kp, fl, sel, frames, vp, s); break;
+    case 8: launch_fwd_t<T, 8>(vol, A, B, geo, out, valid, status, counter, kp, fl, sel, frames, vp, s); break;
     default: return DIFFUS_E_PLAN;
     }
     return DIFFUS_OK;
@@ -372,7 +498,7 @@ extern "C" size_t diffus_batch_plan_bytes(const diffus_fan *fans, int32_t P)
         total_rays += fans[p].n_rays;
     }
     if (total_rays > INT32_MAX) return 0;
-    return (size_t)plan_sizes(P, total_rays, count_tiles(fans, P)).bytes;
+    return (size_t)plan_sizes(P, total_rays, count_tiles(fans, P), count_ftiles(fans, P)).bytes;
 }
 
 extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan *fans, int32_t P,
@@ -398,11 +524,12 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
         max_depth = std::max(max_depth, fans[p].depth_mm);
     }
     if (total_rays > INT32_MAX) return DIFFUS_E_DIMS;
-    const int64_t n_tiles = count_tiles(fans, P);
-    PlanSizes z = plan_sizes(P, total_rays, n_tiles);
+    const int64_t n_tiles = count_tiles(fans, P), n_ftiles = count_ftiles(fans, P);
+    PlanSizes z = plan_sizes(P, total_rays, n_tiles, n_ftiles);
     if (plan_bytes < (size_t)z.bytes) return DIFFUS_E_WORKSPACE;
 
     diffus_schedule sc = sched ? *sched : diffus_schedule{0, 0, 0, 0};
+    if (sc.fwd_form != 0 && sc.fwd_form != 1) return DIFFUS_E_PARAM;
     if (sc.rays_per_cta == 0) sc.rays_per_cta = 4;
     if (sc.ctas_per_sm == 0) sc.ctas_per_sm = 4;
     if (sc.brick == 0) sc.brick = 8;    // gather CTAs per SM
@@ -418,15 +545,23 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     H.total_gz = total_gz;
     H.total_ckpt = total_ck;
     H.n_tiles = n_tiles;
+    H.n_ftiles = n_ftiles;
+    {
+        int64_t tb = 0;
+        for (int p = 0; p < P; p++)
+            tb += (int64_t)fans[p].n_rays * ((fans[p].n_samples + kCarryRows - 1) / kCarryRows);
+        H.total_bcar = tb;
+    }
     H.max_S = max_S;
     H.max_depth = max_depth;
     H.blurW = blur_halfwidth(prm);
     H.warps = sc.rays_per_cta;
     H.ctas_per_sm = sc.ctas_per_sm;
     H.gather_ctas = sc.brick;
+    H.fwd_form = sc.fwd_form;
     H.off_pose = z.off[0]; H.off_depth = z.off[1]; H.off_ray0 = z.off[2]; H.off_ray_pose = z.off[3];
     H.off_ray_j = z.off[4]; H.off_order = z.off[5]; H.off_row_off = z.off[6]; H.off_gz_off = z.off[7];
-    H.off_ck_off = z.off[8]; H.off_tiles = z.off[9];
+    H.off_ck_off = z.off[8]; H.off_tiles = z.off[9]; H.off_ftiles = z.off[10];
     H.bytes = z.bytes;
     H.params_fp = params_fingerprint(prm);
 
@@ -440,10 +575,20 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     int64_t *gz_off = at_mut<int64_t>(plan_host, H.off_gz_off);
     int64_t *ck_off = at_mut<int64_t>(plan_host, H.off_ck_off);
     BlurTile *tiles = at_mut<BlurTile>(plan_host, H.off_tiles);
+    TileDesc *ftiles = at_mut<TileDesc>(plan_host, H.off_ftiles);
 
-    int64_t r = 0, img = 0, g = 0, ck = 0, t = 0;
+    int64_t r = 0, img = 0, g = 0, ck = 0, t = 0, ft = 0, cb = 0;
     for (int p = 0; p < P; p++) {
         const diffus_fan &f = fans[p];
+        {
+            const int nseg_p = (f.n_samples + kSeg - 1) / kSeg;
+            const int ncar_p = (f.n_samples + kCarryRows - 1) / kCarryRows;
+            for (int j0 = 0; j0 < f.n_rays; j0 += kWarp)
+                ftiles[ft++] = TileDesc{p, j0, std::min(kWarp, f.n_rays - j0), f.n_samples,
+                                        img + (int64_t)j0 * f.n_samples, g + (int64_t)j0 * (f.n_samples + 1),
+                                        ck + (int64_t)j0 * nseg_p, cb + (int64_t)j0 * ncar_p, (int32_t)(r + j0), 0};
+            cb += (int64_t)f.n_rays * ncar_p;
+        }
         double a = attenuation_a(&f);
         float hi, lo;
         gain_l2(a, hi, lo);
@@ -472,10 +617,12 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     std::stable_sort(ord.begin(), ord.end(),
                      [&](int32_t x, int32_t y) { return pp[ray_pose[x]].S > pp[ray_pose[y]].S; });
     std::copy(ord.begin(), ord.end(), order);
+    // forward tiles longest first (ties in plan order)
+    std::stable_sort(ftiles, ftiles + n_ftiles, [](const TileDesc &x, const TileDesc &y) { return x.S > y.S; });
     // blur strips of the widest poses first (a strip's work grows with n_rays)
     std::stable_sort(tiles, tiles + n_tiles, [](const BlurTile &x, const BlurTile &y) { return x.n_rays > y.n_rays; });
 
-    BatchLayout L = batch_layout(nullptr, H, vd, prm->blur != 0, prm->speckle != 0, prm->atten != 0);
+    BatchLayout L = batch_layout(nullptr, H, vd, prm->blur != 0, prm->speckle != 0, prm->atten != 0, prm->refine != 0);
     if (ws_fwd) *ws_fwd = L.fwd_bytes;
     if (ws_bwd) *ws_bwd = L.bytes;
     return DIFFUS_OK;
@@ -500,7 +647,7 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
         ((uintptr_t)workspace) % 256 || ((uintptr_t)plan_dev) % 256)
         return DIFFUS_E_ALIGN;
     const bool bwd = grad_images != nullptr;
-    BatchLayout L = batch_layout(workspace, H, vd, prm->blur != 0, prm->speckle != 0, prm->atten != 0);
+    BatchLayout L = batch_layout(workspace, H, vd, prm->blur != 0, prm->speckle != 0, prm->atten != 0, prm->refine != 0);
     if (ws_bytes < (bwd ? L.bytes : L.fwd_bytes)) return DIFFUS_E_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -522,7 +669,7 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     B.total_rays = H.total_rays;
 
     if (status && cudaMemsetAsync(status, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
-    if (cudaMemsetAsync(L.counter, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
+    if (cudaMemsetAsync(L.counter, 0, 8 * sizeof(unsigned), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
     mark(DIFFUS_TR_START);
     k_pose_frames<<<(H.P + 127) / 128, 128, 0, s>>>(poses, H.P, L.frames);
     k_batch_setup<<<(unsigned)((H.total_rays + 127) / 128), 128, 0, s>>>(L.frames, B, make_place(vd), L.geo);
@@ -539,13 +686,17 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     // (the adjoint samples dZ/dp itself only in a pose-only call)
     const bool march_pose = grad_poses && !grad_vol;
     const bool keep_samples = bwd && !march_pose;
-    const FwdKeep kp{bwd ? L.ckpt : nullptr, bwd ? L.mbuf : nullptr, keep_samples ? L.kbuf : nullptr};
+    const FwdKeep kp{bwd ? L.ckpt : nullptr, bwd ? L.mbuf : nullptr, keep_samples ? L.kbuf : nullptr,
+                     keep_samples ? L.bcar : nullptr};
+    const VolPlace vp = make_place(vd);
+    FwdLaunch fl{grid, H.fwd_form, at<TileDesc>(plan_dev, H.off_ftiles), H.n_ftiles};
+    if (H.fwd_form == 0) fl.grid = sm_count() * std::max(1, H.ctas_per_sm * H.warps / kTileWarps);
     if (vd->dtype == DIFFUS_F32)
-        rc = launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0, kp, grid,
-                                 prm->refine != 0, s);
+        rc = launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0, kp, fl,
+                                 L.sel, L.frames, vp, s);
     else
         rc = launch_fwd_w<unsigned short>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0,
-                                          kp, grid, prm->refine != 0, s);
+                                          kp, fl, L.sel, L.frames, vp, s);
     if (rc) return rc;
     const int rgrid = (int)std::min<int64_t>((H.total_rays + 7) / 8, (int64_t)sm_count() * 16);
     // the depth gain rides on the blur's output; without blur it is a row pass
@@ -578,7 +729,13 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     mark(DIFFUS_TR_MARCH_BWD);
     // with a volume gradient the gather also forms the pose terms, so the
     // adjoint march reads the kept samples (march_pose above)
-    if (vd->dtype == DIFFUS_F32)
+    if (H.fwd_form == 0 && !march_pose) {
+        // six 2-warp CTAs (two input stages each) fill an SM's shared memory
+        const int bgrid = sm_count() * 6;
+        k_batch_bwd_tiles<<<bgrid, kTileWarpsBwd * 32, 0, s>>>(A, B, at<TileDesc>(plan_dev, H.off_ftiles), H.n_ftiles, gy,
+                                                            L.mbuf, L.kbuf, L.bcar, L.gz, L.counter + 1);
+        rc = DIFFUS_OK;
+    } else if (vd->dtype == DIFFUS_F32)
         rc = launch_bwd_w<float>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, L.mbuf, L.kbuf,
                                  grid, march_pose, s);
     else

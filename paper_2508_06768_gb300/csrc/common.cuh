@@ -53,6 +53,9 @@ struct Speckle {
     int on;
     uint32_t key0, key1;
     uint32_t pose_ctr;
+    int Lr;                // radial half-length (0..4)
+    float nr_scale;        // sqrt(3)/256 / sqrt(2 Lr + 1): byte-sum window -> radial normal
+    uint32_t rk[20];       // Philox round keys of (key0, key1), two per round
 };
 
 // ---------------------------------------------------------------- volume
@@ -93,11 +96,13 @@ __device__ __forceinline__ void sample_z(const T *__restrict__ vol, const VolGeo
     axis_split(Y, g.ny, iy, fy, iny);
     axis_split(Zc, g.nz, iz, fz, inz);
     const unsigned sy = (unsigned)g.nx, sz = (unsigned)g.nx * (unsigned)g.ny;
-    const unsigned o = (unsigned)iz * sz + (unsigned)iy * sy + (unsigned)ix;
-    float c000 = ldv(vol, o), c100 = ldv(vol, o + 1);
-    float c010 = ldv(vol, o + sy), c110 = ldv(vol, o + sy + 1);
-    float c001 = ldv(vol, o + sz), c101 = ldv(vol, o + sz + 1);
-    float c011 = ldv(vol, o + sz + sy), c111 = ldv(vol, o + sz + sy + 1);
+    // one row pointer per (y, z) corner pair; the x neighbour is the next element
+    const T *__restrict__ p00 = vol + ((unsigned)iz * sz + (unsigned)iy * sy + (unsigned)ix);
+    const T *__restrict__ p10 = p00 + sy, *__restrict__ p01 = p00 + sz, *__restrict__ p11 = p01 + sy;
+    float c000 = ldv(p00, 0), c100 = ldv(p00, 1);
+    float c010 = ldv(p10, 0), c110 = ldv(p10, 1);
+    float c001 = ldv(p01, 0), c101 = ldv(p01, 1);
+    float c011 = ldv(p11, 0), c111 = ldv(p11, 1);
     float d1 = c100 - c000, d2 = c010 - c000, d3 = c110 - c000;
     float d4 = c001 - c000, d5 = c101 - c000, d6 = c011 - c000, d7 = c111 - c000;
     float e00 = fx * d1;
@@ -123,6 +128,43 @@ __device__ __forceinline__ void sample_z(const T *__restrict__ vol, const VolGeo
         grad[1] = iny ? gy * g.isy : 0.0f;
         grad[2] = inz ? gz * g.isz : 0.0f;
     }
+}
+
+// Impedance in FP64 for the residual of the refinement pass: the trilinear
+// form of the cell that the fixed-point position (X, Y, Zc) selects, with
+// FP64 lerps of the stored corners and FP64 weights taken from the ray's
+// FP64 position p (voxel coordinates of the same sample without the
+// fixed-point rounding, as the FP64 definition samples it).  An axis whose
+// fixed-point coordinate is clamped (outside [0, n-1]) keeps the clamped
+// weight 0 or 1.  Near a cell face the two positions may select
+// neighbouring cells; the trilinear field is continuous there, so the value
+// moves only by the rounding distance times the jump of its slope.
+__device__ __forceinline__ double axis_w64(long long X, int n, double x, int &i0)
+{
+    const int hi = (int)(X >> 32);
+    const bool below = X < 0, above = hi >= n - 1;
+    i0 = below ? 0 : (above ? n - 2 : hi);
+    return below ? 0.0 : (above ? 1.0 : x - (double)i0);
+}
+
+template <typename T>
+__device__ __forceinline__ double sample_z64(const T *__restrict__ vol, const VolGeo &g, long long X, long long Y,
+                                             long long Zc, double px, double py, double pz)
+{
+    int ix, iy, iz;
+    const double fx = axis_w64(X, g.nx, px, ix);
+    const double fy = axis_w64(Y, g.ny, py, iy);
+    const double fz = axis_w64(Zc, g.nz, pz, iz);
+    const unsigned sy = (unsigned)g.nx, sz = (unsigned)g.nx * (unsigned)g.ny;
+    const unsigned o = (unsigned)iz * sz + (unsigned)iy * sy + (unsigned)ix;
+    const double c000 = ldv(vol, o), c100 = ldv(vol, o + 1);
+    const double c010 = ldv(vol, o + sy), c110 = ldv(vol, o + sy + 1);
+    const double c001 = ldv(vol, o + sz), c101 = ldv(vol, o + sz + 1);
+    const double c011 = ldv(vol, o + sz + sy), c111 = ldv(vol, o + sz + sy + 1);
+    const double c00 = fma(fx, c100 - c000, c000), c10 = fma(fx, c110 - c010, c010);
+    const double c01 = fma(fx, c101 - c001, c001), c11 = fma(fx, c111 - c011, c011);
+    const double c0 = fma(fy, c10 - c00, c00), c1 = fma(fy, c11 - c01, c01);
+    return fma(fz, c1 - c0, c0);
 }
 
 // Round-trip depth gain a^(2(k+1)) = 2^((k+1) l2) of echo row k under the
@@ -268,6 +310,21 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// The same generator with the round keys precomputed (they depend on the
+// seed only): rk[2r], rk[2r+1] are the key words of round r.  Passed in
+// kernel parameters, the keys are operands of the round's xor, so the key
+// schedule costs nothing per call.
+__device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t *rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * r], lo1, hi0 ^ c.w ^ rk[2 * r + 1], lo0);
     }
     return c;
 }

@@ -107,6 +107,16 @@ inline Speckle make_speckle(const diffus_params *p)
     s.key0 = (uint32_t)(p->seed & 0xffffffffu);
     s.key1 = (uint32_t)(p->seed >> 32);
     s.pose_ctr = p->pose_ctr;
+    s.Lr = p->Lr;
+    s.nr_scale = (float)(sqrt(3.0) / 256.0 / sqrt(2.0 * p->Lr + 1.0));
+    // Philox4x32-10 key schedule (Weyl increments of Salmon et al.)
+    uint32_t k0 = s.key0, k1 = s.key1;
+    for (int r = 0; r < 10; r++) {
+        s.rk[2 * r] = k0;
+        s.rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
     return s;
 }
 

@@ -84,24 +84,35 @@ static __global__ void k_pose_frames(const float *__restrict__ poses, int P, Pos
     frames[p] = f;
 }
 
+// FP64 voxel coordinates of sample 0 of ray `ray` and the step between
+// samples (Section 2.4): sample k lies at x0 + k dx = (t + (k + 1/2) ds u -
+// origin) / spacing.  st, ct: sin and cos of the beam angle.
+__device__ __forceinline__ void ray_line(const PoseFrame &f, int ray, const FanDev &fan, const VolPlace &vp,
+                                         double x0[3], double dx[3], double &st, double &ct)
+{
+    double th = fan.n_rays > 1 ? -0.5 * fan.fov + fan.fov * (double)ray / (double)(fan.n_rays - 1) : 0.0;
+    sincos(th, &st, &ct);
+    double ds = fan.depth / (double)fan.S;
+    double sp[3] = {vp.sx, vp.sy, vp.sz}, org[3] = {vp.ox, vp.oy, vp.oz};
+    for (int i = 0; i < 3; i++) {
+        const double u = f.Rc[i][0] * st + f.Rc[i][1] * ct;
+        x0[i] = (f.t[i] + 0.5 * ds * u - org[i]) / sp[i];
+        dx[i] = ds * u / sp[i];
+    }
+}
+
 // Geometry of ray `ray` of pose `pose_idx` (Section 2.4): FP64 direction and
 // fixed-point positions, exactly t + (k + 1/2) ds u in voxel coordinates.
 __device__ __forceinline__ void setup_ray(const PoseFrame &f, int pose_idx, int ray, const FanDev &fan,
                                           const VolPlace &vp, RayGeo &out)
 {
-    double th = fan.n_rays > 1 ? -0.5 * fan.fov + fan.fov * (double)ray / (double)(fan.n_rays - 1) : 0.0;
-    double st, ct;
-    sincos(th, &st, &ct);
-    double u[3];
-    for (int i = 0; i < 3; i++) u[i] = f.Rc[i][0] * st + f.Rc[i][1] * ct;
-    double ds = fan.depth / (double)fan.S;
-    double sp[3] = {vp.sx, vp.sy, vp.sz}, org[3] = {vp.ox, vp.oy, vp.oz};
+    double x0[3], dx[3], st, ct;
+    ray_line(f, ray, fan, vp, x0, dx, st, ct);
     for (int i = 0; i < 3; i++) {
-        double x0 = (f.t[i] + 0.5 * ds * u[i] - org[i]) / sp[i];
-        double dx = ds * u[i] / sp[i];
-        out.X0[i] = to_fixed(x0);
-        out.DX[i] = __double2ll_rn(dx * 4294967296.0);
+        out.X0[i] = to_fixed(x0[i]);
+        out.DX[i] = __double2ll_rn(dx[i] * 4294967296.0);
     }
+    const double ds = fan.depth / (double)fan.S;
     for (int q = 0; q < 3; q++)
         for (int i = 0; i < 3; i++) out.v[q][i] = (float)(f.dRc[q][i][0] * st + f.dRc[q][i][1] * ct);
     out.pose = pose_idx;
@@ -123,20 +134,73 @@ static __global__ void k_ray_setup(const PoseFrame *__restrict__ frame, FanDev f
 // One warp per ray, kWarpsFwd warps per CTA.
 constexpr int kWarpsFwd = 4;
 
-template <typename T, bool REFINE>
+// Where the FP32 pass records the rays that need the refined pass (all null
+// when refinement is off): per ray (segments to refine, first ill-posed depth
+// of the FP32 pass), the list of such rays, its length and the refined
+// pass's ticket counter.
+struct RefineSel {
+    int2 *rinfo;
+    int *rlist;
+    unsigned *rcount;
+    unsigned *ticket;
+};
+
+template <typename T>
 __global__ void __launch_bounds__(kWarpsFwd * 32) k_march_fwd(const T *__restrict__ vol, MarchArgs A,
                                                               const RayGeo *__restrict__ geo, int n_rays,
                                                               float *__restrict__ out, int *__restrict__ valid,
-                                                              uint32_t *__restrict__ status)
+                                                              uint32_t *__restrict__ status, RefineSel sel)
 {
     __shared__ float buf[kWarpsFwd][kSegPad];
-    __shared__ double dbuf[REFINE ? kWarpsFwd : 1][REFINE ? kSegPad : 1];
     const int w = threadIdx.x >> 5;
     const int j = blockIdx.x * kWarpsFwd + w;
     if (j >= n_rays) return;
     RayGeo rg = geo[j];
-    RayOut o{out + (size_t)j * rg.S, valid ? valid + j : nullptr, status, nullptr, nullptr};
-    march_fwd_ray<T, REFINE>(vol, A, rg, o, buf[w], REFINE ? dbuf[w] : nullptr);
+    RayOut o{out + (size_t)j * rg.S, valid ? valid + j : nullptr, status, nullptr, nullptr, nullptr,
+             sel.rinfo ? sel.rinfo + j : nullptr, sel.rlist, sel.rcount, j};
+    march_fwd_ray<T>(vol, A, rg, o, buf[w]);
+}
+
+// The refined pass of one ray that the FP32 pass listed: its FP64 line from
+// the pose frame, then the refined march over the segments it recorded.
+template <typename T, bool STREAM>
+__device__ __forceinline__ void refine_ray(const T *__restrict__ vol, const MarchArgs &A, const RayGeo &rg,
+                                           const PoseFrame &f, const FanDev &fan, const VolPlace &vp,
+                                           const RayOut &out, int2 info, float *buf, double *dbuf)
+{
+    RayLine64 line;
+    double st, ct;
+    ray_line(f, rg.ray, fan, vp, line.x0, line.dx, st, ct);
+    march_fwd_ray<T, true, STREAM>(vol, A, rg, out, buf, dbuf, &line, info);
+}
+
+// Refined pass of one pose: each warp takes listed rays from the ticket
+// counter until the list (whose length the FP32 pass left in *rcount) is done.
+template <typename T>
+__global__ void __launch_bounds__(kWarpsFwd * 32, 1) k_march_refine(const T *__restrict__ vol, MarchArgs A,
+                                                                    const RayGeo *__restrict__ geo,
+                                                                    const PoseFrame *__restrict__ frame, FanDev fan,
+                                                                    VolPlace vp, float *__restrict__ out,
+                                                                    int *__restrict__ valid,
+                                                                    uint32_t *__restrict__ status, RefineSel sel)
+{
+    __shared__ float buf[kWarpsFwd][kSegPad];
+    __shared__ double dbuf[kWarpsFwd][kSegPad];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned n = *sel.rcount;
+    const PoseFrame f = *frame;
+    for (;;) {
+        unsigned q = 0;
+        if (lane == 0) q = atomicAdd(sel.ticket, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= n) break;
+        const int j = sel.rlist[q];
+        const RayGeo rg = geo[j];
+        RayOut o{out + (size_t)j * rg.S, valid ? valid + j : nullptr, status, nullptr, nullptr, nullptr,
+                 nullptr, nullptr, nullptr, j};
+        refine_ray<T, false>(vol, A, rg, f, fan, vp, o, sel.rinfo[j], buf[w], dbuf[w]);
+        __syncwarp();
+    }
 }
 
 // ------------------------------------------------------------------ blur

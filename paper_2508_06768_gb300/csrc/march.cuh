@@ -30,6 +30,24 @@ struct MarchArgs {
     Speckle sp;
 };
 
+// Selective refinement.  The FP32 pass marks a row as needing the refined
+// pass when its conditioning md = min(det(A_k), det(A_{k+1})) falls below
+// max(kNeedFloor, kNeedCoef sqrt(S)).  The FP32 error of an echo row grows
+// like c sqrt(S) / md with c ~ 2.5e-8, measured against the FP64 definition
+// (5e-7 / md at 256 samples, 1.6e-6 / md at 4096): kNeedCoef sqrt(S) is where
+// that estimate reaches the 1e-5 tolerance, and kNeedFloor is the
+// conditioning below which the FP32 path is not held to the tolerance at
+// all.  A ray with a pole is refined up to the pole's row, whose decision
+// the refined pass takes again.
+constexpr float kNeedCoef = 0.0025f;
+constexpr float kNeedFloor = 0.05f;
+
+// FP64 line of one ray (voxel coordinates of sample 0 and the step), for the
+// samples of the refined pass.
+struct RayLine64 {
+    double x0[3], dx[3];
+};
+
 struct RayOut {
     float *row;       // output row [S] (image or pre-blur buffer)
     int *valid;       // nullable: leading pole-free rows
@@ -37,6 +55,11 @@ struct RayOut {
     float4 *ckpt;     // nullable: scan carry (b0, b1, D) at every segment start, for the adjoint
     float *mrow;      // nullable: speckle factor of every row, for the adjoint
     float2 *krow;     // nullable: per sample k = 0..S, (zref + dz, r_{k-1}) for the adjoint (r_{-1} = 0)
+    // selective refinement (FP32 pass; all null when refinement is off):
+    int2 *rinfo;      // this ray's (segments for the refined pass, first ill-posed depth of the FP32 pass)
+    int *rlist;       // rays that need the refined pass are appended here ...
+    unsigned *rcount; // ... at this counter
+    int rid;          // this ray's index in rinfo / rlist
 };
 
 __device__ __forceinline__ int smem_idx(int x) { return x + (x >> 3); }
@@ -52,14 +75,19 @@ __device__ __forceinline__ void sample_pos(const RayGeo &rg, int k, long long &X
 // writes r_i (i = base..base+255, 0 past the ray) into buf[smem_idx(i-base)].
 // (czr, cdz) carries the sample at `base` in and the one at base+256 out.
 // krow (nullable) also receives, per sample k, (zref + dz, r_{k-1}).
+// REFINE (the refined pass) also writes r_i in FP64 into dbuf, from FP64
+// samples (sample_z64) at the FP64 positions of `line`; cz64 carries the
+// FP64 sample at `base` in and the one at base+256 out.
 template <typename T, bool REFINE = false>
 __device__ __forceinline__ void seg_reflections(const T *__restrict__ vol, const VolGeo &g, const RayGeo &rg,
                                                 int base, float &czr, float &cdz, float *__restrict__ buf,
-                                                double *__restrict__ dbuf = nullptr, float2 *__restrict__ krow = nullptr)
+                                                double *__restrict__ dbuf = nullptr, float2 *__restrict__ krow = nullptr,
+                                                const RayLine64 *line = nullptr, double *cz64 = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int S = rg.S;
     float pzr = czr, pdz = cdz;
+    double pz64 = REFINE ? *cz64 : 0.0;
     long long X, Y, Z;
     sample_pos(rg, base + lane + 1, X, Y, Z);
     const long long sX = rg.DX[0] * kWarp, sY = rg.DX[1] * kWarp, sZ = rg.DX[2] * kWarp;
@@ -67,7 +95,15 @@ __device__ __forceinline__ void seg_reflections(const T *__restrict__ vol, const
     for (int t = 0; t < kChunk; t++) {
         int k = base + t * kWarp + lane + 1;
         float zr = 0.0f, dz = 0.0f;
-        if (k <= S) sample_z<T, false>(vol, g, X, Y, Z, zr, dz);
+        double z64 = 0.0;
+        if (k <= S) {
+            sample_z<T, false>(vol, g, X, Y, Z, zr, dz);
+            if (REFINE) {
+                const double kd = (double)k;
+                z64 = sample_z64<T>(vol, g, X, Y, Z, fma(kd, line->dx[0], line->x0[0]),
+                                    fma(kd, line->dx[1], line->x0[1]), fma(kd, line->dx[2], line->x0[2]));
+            }
+        }
         X += sX;
         Y += sY;
         Z += sZ;
@@ -77,12 +113,18 @@ __device__ __forceinline__ void seg_reflections(const T *__restrict__ vol, const
         float r = (k - 1 < S) ? refl(lzr, ldz, zr, dz) : 0.0f;
         buf[smem_idx(t * kWarp + lane)] = r;
         if (krow && k <= S) __stcs(krow + k, make_float2(zr + dz, r));
-        if (REFINE) dbuf[smem_idx(t * kWarp + lane)] = (k - 1 < S) ? refl64(lzr, ldz, zr, dz) : 0.0;
+        if (REFINE) {
+            double lz64 = __shfl_up_sync(0xffffffffu, z64, 1);
+            if (lane == 0) lz64 = pz64;
+            dbuf[smem_idx(t * kWarp + lane)] = (k - 1 < S) ? (z64 - lz64) / (z64 + lz64) : 0.0;
+            pz64 = __shfl_sync(0xffffffffu, z64, 31);
+        }
         pzr = __shfl_sync(0xffffffffu, zr, 31);
         pdz = __shfl_sync(0xffffffffu, dz, 31);
     }
     czr = pzr;
     cdz = pdz;
+    if (REFINE) *cz64 = pz64;
 }
 
 // Chunk product Q = M_{i0} ... M_{i0+7} (identity past the ray) and its
@@ -165,7 +207,7 @@ __device__ __forceinline__ void warp_scan_affine(Mat2 Q, float dq, float &c0, fl
 // Radial white normals of group q (4 rows 4q..4q+3), stream 0.
 __device__ __forceinline__ uint4 radial_group(const Speckle &sp, int q, int ray, uint32_t pose)
 {
-    return philox10(make_uint4((uint32_t)q, (uint32_t)ray, pose, 0u), sp.key0, sp.key1);
+    return philox10_rk(make_uint4((uint32_t)q, (uint32_t)ray, pose, 0u), sp.rk);
 }
 
 __device__ __forceinline__ uint4 shfl_up_u4(uint4 v, int off)
@@ -215,7 +257,7 @@ __device__ __forceinline__ void chunk_speckle(const Speckle &sp, int i0, int S, 
             uint32_t cell = grain_cell(i, kb1, kb2, kb3, sp.gshift);
             uint32_t grp = cell >> 2;
             if (grp != cur_grp) {
-                gw = philox10(make_uint4(grp, (uint32_t)ray, pose, 1u), sp.key0, sp.key1);
+                gw = philox10_rk(make_uint4(grp, (uint32_t)ray, pose, 1u), sp.rk);
                 cur_grp = grp;
             }
             float ng = ih_normal(pick4(gw, cell & 3u));
@@ -228,34 +270,60 @@ __device__ __forceinline__ void chunk_speckle(const Speckle &sp, int i0, int S, 
 // kSegPad floats; dbuf: kSegPad doubles when REFINE.  STREAM writes the
 // output row with evict-first stores (the batched kernel).
 //
-// REFINE adds one iterative-refinement pass of the depth recurrence
-// b_{i+1} = b_i M_i, D_{i+1} = D_i delta_i per segment: the FP32 states are
-// kept, their residuals rho_{i+1} = b_i M_i - b_{i+1} are computed in FP64
-// with M_i recomputed in FP64 from the same samples, the error recurrence
+// Without REFINE (the FP32 pass) and with out.rinfo set, the march also
+// decides whether the ray needs the refined pass (rows whose md falls below
+// kNeedCoef sqrt(S), or a pole): such a ray is appended to out.rlist, and its
+// valid-row count and status are left to the refined pass.
+//
+// REFINE (the refined pass, line = the ray's FP64 line, rinfo = what the FP32
+// pass recorded) redoes the first segments of the ray with one
+// iterative-refinement pass of the depth recurrence b_{i+1} = b_i M_i,
+// D_{i+1} = D_i delta_i: the FP32 states are kept, their residuals
+// rho_{i+1} = b_i M*_i - b_{i+1} are computed in FP64 with M*_i the FP64
+// coefficients of FP64 samples (sample_z64), the error recurrence
 // e_{i+1} = e_i M_i + rho_{i+1} (e_0 = 0) of e_i = b*_i - b_i (b* the states
 // of the FP64 coefficients) is solved in FP32 with the same scan (affine
-// maps), and the echoes use the corrected states b_i + e_i.
+// maps), and the echoes use the corrected states b_i + e_i and the FP64
+// coefficient x*_i.  It covers rinfo.x segments, and goes on while the FP32
+// pass saw a pole there that the refined states do not confirm; rows beyond
+// keep the FP32 pass's values.
 template <typename T, bool REFINE = false, bool STREAM = false>
 __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, const RayGeo &rg,
-                              const RayOut &out, float *__restrict__ buf, double *__restrict__ dbuf = nullptr)
+                              const RayOut &out, float *__restrict__ buf, double *__restrict__ dbuf = nullptr,
+                              const RayLine64 *line = nullptr, int2 rinfo = make_int2(0, 0))
 {
     const int lane = threadIdx.x & 31;
     const int S = rg.S;
     const uint32_t pose = A.sp.pose_ctr + (uint32_t)rg.pose;
+    const int nseg = (S + kSeg - 1) / kSeg;
 
     float czr, cdz;
     sample_z<T, false>(vol, A.g, rg.X0[0], rg.X0[1], rg.X0[2], czr, cdz);
-    if (out.krow && lane == 0) out.krow[0] = make_float2(czr + cdz, 0.0f);
+    double cz64 = 0.0;
+    if (REFINE)
+        cz64 = sample_z64<T>(vol, A.g, rg.X0[0], rg.X0[1], rg.X0[2], line->x0[0], line->x0[1], line->x0[2]);
+    if (!REFINE && out.krow && lane == 0) out.krow[0] = make_float2(czr + cdz, 0.0f);
     float bs0 = 0.0f, bs1 = 1.0f, Ds = 1.0f;   // bottom row and det at segment start
     int first_bad = 0x7fffffff;
     int nonfinite = 0;
+    int last_need = -1;                         // FP32 pass: last row with md below the threshold
+    const float need_md = fmaxf(kNeedFloor, kNeedCoef * sqrtf((float)S));
     const bool vec4 = ((((uintptr_t)out.row) & 15) == 0);
 
     float es0 = 0.0f, es1 = 0.0f, esD = 0.0f;  // refinement: correction at segment start
-
-    for (int base = 0; base < S; base += kSeg) {
-        if (out.ckpt && lane == 0) out.ckpt[base / kSeg] = make_float4(bs0 + es0, bs1 + es1, Ds + esD, 0.0f);
-        seg_reflections<T, REFINE>(vol, A.g, rg, base, czr, cdz, buf, dbuf, out.krow);
+    // REFINE: segments to redo; extended while the FP32 pass's pole lies
+    // before the end and the refined states have not found one
+    const bool fp32_pole = rinfo.y <= S;
+    int seg = 0;
+    for (; seg < nseg; seg++) {
+        if (REFINE && seg >= rinfo.x) {
+            const bool pole_seen = __shfl_sync(0xffffffffu, first_bad, 0) <= S;   // lane 0 holds the reduced value
+            if (!(fp32_pole && !pole_seen)) break;
+        }
+        const int base = seg * kSeg;
+        if (out.ckpt && lane == 0) out.ckpt[seg] = make_float4(bs0 + es0, bs1 + es1, Ds + esD, 0.0f);
+        seg_reflections<T, REFINE>(vol, A.g, rg, base, czr, cdz, buf, dbuf, REFINE ? nullptr : out.krow, line,
+                                   &cz64);
         __syncwarp();
         const int i0 = base + lane * kChunk;
         float rr[kChunk];
@@ -282,7 +350,7 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
 #pragma unroll
             for (int t = 0; t < kChunk; t++) m[t] = 1.0f;
         }
-        if (out.mrow) {
+        if (!REFINE && out.mrow) {
 #pragma unroll
             for (int t = 0; t < kChunk; t++)
                 if (i0 + t < S) __stcs(out.mrow + i0 + t, m[t]);
@@ -298,6 +366,7 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                     float q = fmaf(b0, x.m01, b1);          // det(A_{i+1})
                     float e = x.m01 * D * frcp(b1 * q);
                     if (!(q >= kPoleEps)) first_bad = min(first_bad, i + 1);
+                    if (fminf(b1, q) < need_md) last_need = i;
                     float nb0 = fmaf(b0, x.m00, b1 * x.m10);
                     b1 = q;
                     b0 = nb0;
@@ -342,18 +411,20 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                 }
             }
             // FP64 residuals and the chunk's local correction map e -> e Q + c
-            float rho0[kChunk], rho1[kChunk], rhoD[kChunk];
+            float rho0[kChunk], rho1[kChunk], rhoD[kChunk], xs[kChunk];
             float c0 = 0.0f, c1 = 0.0f, cD = 0.0f;
 #pragma unroll
             for (int t = 0; t < kChunk; t++) {
                 rho0[t] = rho1[t] = rhoD[t] = 0.0f;
+                xs[t] = 0.0f;
                 if (i0 + t < S) {
                     const Xfer64 x = xfer64(dbuf[smem_idx(lane * kChunk + t)], A.a2d, A.mode);
                     const double p0 = sb0[t], p1 = sb1[t];
-                    // rho = b_i M_i - b_{i+1}: what the FP32 step lost
+                    // rho = b_i M*_i - b_{i+1}: what the FP32 step lost
                     rho0[t] = (float)(fma(p0, x.m00, p1 * x.m10) - (double)sb0[t + 1]);
                     rho1[t] = (float)(fma(p0, x.m01, p1) - (double)sb1[t + 1]);
                     rhoD[t] = (float)((double)sD[t] * x.delta - (double)sD[t + 1]);
+                    xs[t] = (float)x.m01;
                     const Xfer xf = xfer(rr[t], A.a2, A.mode);
                     const float n0 = fmaf(c0, xf.m00, fmaf(c1, xf.m10, rho0[t]));
                     c1 = fmaf(c0, xf.m01, c1 + rho1[t]);
@@ -386,7 +457,7 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                     e0 = n0;
                     eD = fmaf(eD, x.delta, rhoD[t]);
                     const float q = sb1[t + 1] + e1;                   // corrected det(A_{i+1})
-                    const float e = x.m01 * cDv * frcp(cb1 * q);
+                    const float e = xs[t] * cDv * frcp(cb1 * q);
                     if (!(q >= kPoleEps)) first_bad = min(first_bad, i + 1);
                     y[t] = m[t] * e;
                     nonfinite += !isfinite(y[t]);
@@ -414,15 +485,43 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                         out.row[i0 + t] = y[t];
                 }
         }
+        if (REFINE) {   // the pole decision so far, for the loop's stopping rule
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+                first_bad = min(first_bad, __shfl_xor_sync(0xffffffffu, first_bad, off));
+        }
         __syncwarp();
+    }
+    if (REFINE) {
+        // the carry of the first segment the refined pass left alone, so the
+        // adjoint starts from corrected states there too; then the FP32
+        // pass's rows beyond, counted for non-finite values
+        if (seg < nseg && out.ckpt && lane == 0) out.ckpt[seg] = make_float4(bs0 + es0, bs1 + es1, Ds + esD, 0.0f);
+        for (int i = seg * kSeg + lane; i < S; i += kWarp) nonfinite += !isfinite(out.row[i]);
     }
 
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         first_bad = min(first_bad, __shfl_xor_sync(0xffffffffu, first_bad, off));
         nonfinite += __shfl_xor_sync(0xffffffffu, nonfinite, off);
+        if (!REFINE) last_need = max(last_need, __shfl_xor_sync(0xffffffffu, last_need, off));
     }
-    if (lane == 0) {
+    bool defer = false;     // FP32 pass of a ray that the refined pass redoes
+    if (!REFINE && out.rinfo) {
+        // rows up to the pole's (which the refined pass decides again), or
+        // up to the last row whose conditioning needs the refined states
+        const int cover = first_bad <= S ? first_bad - 1 : last_need;
+        const int segs = cover >= 0 ? cover / kSeg + 1 : 0;
+        defer = segs > 0;
+        if (lane == 0) {
+            out.rinfo[0] = make_int2(segs, first_bad <= S ? first_bad : S + 1);
+            if (defer) {
+                out.rlist[atomicAdd(out.rcount, 1u)] = out.rid;
+                if (out.status) atomicAdd(out.status + 3, 1u);
+            }
+        }
+    }
+    if (lane == 0 && !defer) {
         bool bad = first_bad <= S;
         if (out.valid) out.valid[0] = bad ? first_bad - 1 : S;
         if (out.status) {

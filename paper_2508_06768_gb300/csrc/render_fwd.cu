@@ -11,6 +11,7 @@ struct FwdLayout {
     RayGeo *geo;
     PoseFrame *frame;
     float *y;       // pre-blur echo rows (only when blurring)
+    RefineSel sel;  // selective refinement (only with refine = 1)
     size_t bytes;
 };
 
@@ -21,6 +22,13 @@ FwdLayout fwd_layout(void *ws, const diffus_fan *fan, const diffus_params *prm)
     L.geo = c.take<RayGeo>((size_t)fan->n_rays);
     L.frame = c.take<PoseFrame>(1);
     L.y = prm->blur ? c.take<float>((size_t)fan->n_rays * fan->n_samples) : nullptr;
+    L.sel = RefineSel{nullptr, nullptr, nullptr, nullptr};
+    if (prm->refine) {
+        L.sel.rinfo = c.take<int2>((size_t)fan->n_rays);
+        L.sel.rlist = c.take<int>((size_t)fan->n_rays);
+        L.sel.rcount = c.take<unsigned>(2);
+        if (L.sel.rcount) L.sel.ticket = L.sel.rcount + 1;
+    }
     L.bytes = c.used;
     return L;
 }
@@ -65,19 +73,26 @@ int check_common(const void *vol, const diffus_volume_desc *vd, const float *pos
 // when blurring follows).
 int launch_fwd_march(const void *vol, const diffus_volume_desc *vd, const float *pose, const diffus_fan *fan,
                      const diffus_params *prm, RayGeo *geo, PoseFrame *frame, float *out, int32_t *ray_valid,
-                     uint32_t *status, cudaStream_t s)
+                     uint32_t *status, const RefineSel &sel, cudaStream_t s)
 {
     FanDev fd{fan->n_rays, fan->n_samples, fan->fov_rad, fan->depth_mm};
     k_pose_frames<<<1, 32, 0, s>>>(pose, 1, frame);
     k_ray_setup<<<(fan->n_rays + 127) / 128, 128, 0, s>>>(frame, fd, make_place(vd), geo);
     MarchArgs A = make_march_args(vd, fan, prm);
-    int grid = (fan->n_rays + kWarpsFwd - 1) / kWarpsFwd;
-#define DFS_FWD(T, R) \
-    k_march_fwd<T, R><<<grid, kWarpsFwd * 32, 0, s>>>((const T *)vol, A, geo, fan->n_rays, out, ray_valid, status)
+    const int grid = (fan->n_rays + kWarpsFwd - 1) / kWarpsFwd;
+    const bool refine = prm->refine && sel.rinfo;
+    if (refine && cudaMemsetAsync(sel.rcount, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
+    // the FP32 pass, then the refined pass over the rays it listed
+#define DFS_FWD(T)                                                                                               \
+    k_march_fwd<T><<<grid, kWarpsFwd * 32, 0, s>>>((const T *)vol, A, geo, fan->n_rays, out, ray_valid, status, \
+                                                   refine ? sel : RefineSel{nullptr, nullptr, nullptr, nullptr}); \
+    if (refine)                                                                                                  \
+        k_march_refine<T><<<grid, kWarpsFwd * 32, 0, s>>>((const T *)vol, A, geo, frame, fd, make_place(vd), out, \
+                                                          ray_valid, status, sel);
     if (vd->dtype == DIFFUS_F32) {
-        if (prm->refine) DFS_FWD(float, true); else DFS_FWD(float, false);
+        DFS_FWD(float)
     } else {
-        if (prm->refine) DFS_FWD(unsigned short, true); else DFS_FWD(unsigned short, false);
+        DFS_FWD(unsigned short)
     }
 #undef DFS_FWD
     return launch_status();
@@ -131,7 +146,8 @@ extern "C" int diffus_render_fwd(const void *vol, const diffus_volume_desc *vd, 
     cudaStream_t s = (cudaStream_t)stream;
     if (status && cudaMemsetAsync(status, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
     float *march_out = prm->blur ? L.y : image;
-    if ((rc = launch_fwd_march(vol, vd, pose, fan, prm, L.geo, L.frame, march_out, ray_valid, status, s))) return rc;
+    if ((rc = launch_fwd_march(vol, vd, pose, fan, prm, L.geo, L.frame, march_out, ray_valid, status, L.sel, s)))
+        return rc;
     if (prm->atten && !prm->blur) {   // with blur the gain rides on the blur's output
         float hi, lo;
         gain_l2(attenuation_a(fan), hi, lo);

@@ -44,7 +44,8 @@ def test_depth_gain_batch_equals_single_pose():
     fans = I.random_batch_fans(4, seed=41, rays=(5, 30), samples=(100, 700), ds_mm=0.1, fov_deg=40.0)
     prm = I.Params(seed=41, mode=1, atten=1)
     v = torch.from_numpy(vol.data).cuda()
-    r = BatchRenderer(v, vol.spacing, vol.origin, fans, prm, with_bwd=True)
+    # the single-pose path's forward form (one warp per ray): bitwise
+    r = BatchRenderer(v, vol.spacing, vol.origin, fans, prm, with_bwd=True, schedule=B.ScheduleDesc(0, 0, 0, 1))
     Gs = [I.random_weights((f.n_rays, f.n_samples), 70 + p) for p, f in enumerate(fans)]
     r.run(torch.from_numpy(poses).cuda(), torch.from_numpy(np.concatenate([g.ravel() for g in Gs])).cuda())
     torch.cuda.synchronize()

@@ -124,15 +124,18 @@ def test_pose_gradient_with_and_without_volume_gradient(name):
     assert _rel(gp_full, gp_only) <= 2 * GRAD_TOL
 
 
-def test_finite_differences_of_the_cuda_forward():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_finite_differences_of_the_cuda_forward(mode):
     # Central differences (h = 1e-3) of L = sum(G * image) on the CUDA path,
-    # against the same differences of the FP64 oracle.  Trilinear sampling is
+    # against the same differences of the FP64 oracle, in the literal model
+    # of Eq. 1 (mode 0, poles possible: G weights only rows with
+    # min det >= COND_DET_GRAD) and the signed one.  Trilinear sampling is
     # piecewise linear, so at h = 1e-3 mm the quotient averages the slope over
     # the cell faces crossed and differs from the pointwise gradient; both
     # sides cross the same faces, and the oracle pins check the pointwise
     # gradient at h = 1e-6.
     vol, pose, fan, prm = I.workload_small()
-    prm = prm.with_(mode=1)
+    prm = prm.with_(mode=mode)
     G = _loss_weights(vol, pose, fan, prm, seed=5)
     _, gpose = gpu_grad(vol, pose, fan, prm, G)
     h = 1e-3

@@ -46,3 +46,33 @@ def test_noalloc_rejects_requests_beyond_the_scratch():
     img = torch.empty((fan.n_rays, fan.n_samples), device="cuda")
     with pytest.raises(B.DiffusError, match="static scratch"):
         B.render_fwd_noalloc(v, vol.spacing, vol.origin, p, fan, I.Params(), img)
+
+
+def _noalloc_need(n_rays, n_samples, blur):
+    """Forward workspace of diffus_render_fwd: the ray table, the pose frame
+    and, with the blur on, the pre-blur rows, each rounded up to 256 bytes."""
+    a = lambda x: (x + 255) // 256 * 256
+    return a(112 * n_rays) + 256 + (a(4 * n_rays * n_samples) if blur else 0)
+
+
+def test_noalloc_limit_boundary():
+    # the largest accepted blurred fan of 2048 rays renders and matches the
+    # workspace forward; one more sample per ray is rejected before any launch
+    import torch
+    from paper_2508_06768_gb300 import binding as B
+    limit = 16 << 20
+    assert _noalloc_need(2048, 2019, True) <= limit < _noalloc_need(2048, 2020, True)
+    vol = I.small_phantom(n=24, seed=3)
+    v = torch.from_numpy(vol.data).cuda()
+    p = torch.from_numpy(I.top_face_pose(vol)).cuda()
+    prm = I.Params(mode=1, seed=2)
+    fan = I.Fan(2048, 2019, math.radians(60), 20.0)
+    ref, ref_valid, _ = B.render_fwd(v, vol.spacing, vol.origin, p, fan, prm)
+    img = torch.full((fan.n_rays, fan.n_samples), float("nan"), device="cuda")
+    B.render_fwd_noalloc(v, vol.spacing, vol.origin, p, fan, prm, img)
+    torch.cuda.synchronize()
+    assert torch.equal(img, ref)
+    big = I.Fan(2048, 2020, math.radians(60), 20.0)
+    img2 = torch.empty((big.n_rays, big.n_samples), device="cuda")
+    with pytest.raises(B.DiffusError, match="static scratch"):
+        B.render_fwd_noalloc(v, vol.spacing, vol.origin, p, big, prm, img2)
