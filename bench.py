@@ -137,9 +137,14 @@ ALGO_BYTES = {"march_fwd": 4.0, "blur": 8.0, "blur_T": 8.0, "march_bwd": 8.0, "g
 ALGO_OPS = {"march_fwd": 111.0, "march_bwd": 77.0, "gather_units": 45.0}
 BOUND = {"march_fwd": "alu", "march_bwd": "alu", "gather_units": "alu", "blur": "hbm", "blur_T": "hbm"}
 # DRAM bytes per ray-sample measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch over the 64-pose prefix of the
-# workload, divided by its ray-samples); absent where the kernel changed since.
+# dram__bytes_write.sum of one launch over a prefix of the workload (blurs
+# and gather: 64 poses; marches: 192 poses, the forward phase being the
+# speckle kernel plus the march), divided by its ray-samples); absent where
+# the kernel changed since.
 NCU_DRAM_PER_UNIT = {"blur": 6.12, "blur_T": 6.13, "gather_units": 7.44}
+# the marches' figures depend on the forward form (fwd_form 1: one warp per
+# ray; 0: one lane per ray), set from the capture of that form
+NCU_DRAM_PER_UNIT_FORM = {1: {"march_fwd": 18.81, "march_bwd": 19.71}, 0: {"march_fwd": 25.71, "march_bwd": 21.52}}
 
 
 def median_pose_order(fans):
@@ -666,7 +671,10 @@ def run_native(args):
 
     # project autotuner over the persistent schedule (small candidate set)
     sched = None
-    if not args.no_autotune:
+    if args.schedule:
+        w, c, g, f = (int(x) for x in args.schedule.split(","))
+        sched = B.ScheduleDesc(w, c, g, f)
+    elif not args.no_autotune:
         # (warps per CTA, CTAs per SM, gather CTAs per SM, forward form):
         # form 0 runs the marches with one lane per ray (grids of 4-warp CTAs
         # sized from warps x CTAs), form 1 with one warp per ray
@@ -818,7 +826,8 @@ def run_native(args):
     timed = {k: v for k, v in kern_ms.items() if k in BOUND}
     dom = max(timed, key=timed.get)
     t_dom = kern_ms[dom] * 1e-3
-    dram = NCU_DRAM_PER_UNIT.get(dom)
+    form = 1 if sched is None else int(sched.fwd_form)
+    dram = NCU_DRAM_PER_UNIT_FORM[form].get(dom, NCU_DRAM_PER_UNIT.get(dom))
     if BOUND[dom] == "alu":
         ach = ALGO_OPS[dom] * total / t_dom / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": alu_peak, "unit": "Tlane-op/s",
@@ -897,6 +906,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--schedule", default="",
+                    help="warps,ctas_per_sm,gather_ctas,fwd_form for the step instead of the autotuner's pick")
     ap.add_argument("--replicas", action="store_true",
                     help="N>1: every rank renders its own batch (weak scaling) instead of a shard of one job")
     ap.add_argument("--poses", type=int, default=512,

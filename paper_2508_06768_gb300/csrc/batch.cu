@@ -39,12 +39,12 @@ struct BlurTile {                 // one 32-row strip of one pose image
 struct PlanHeader {
     uint32_t magic;
     int32_t P;
-    int64_t total_rays, total_img, total_gz, total_ckpt, n_tiles, n_ftiles, total_bcar;
+    int64_t total_rays, total_img, total_gz, total_ckpt, n_tiles, n_ftiles, total_bcar, n_spk;
     double max_depth;
     int32_t max_S, blurW;
     int32_t warps, ctas_per_sm, gather_ctas, fwd_form;
     int64_t off_pose, off_depth, off_ray0, off_ray_pose, off_ray_j, off_order, off_row_off, off_gz_off, off_ck_off,
-        off_tiles, off_ftiles;
+        off_tiles, off_ftiles, off_spk;
     int64_t bytes;
     uint64_t params_fp;   // fingerprint of the parameters the plan was made for
 };
@@ -70,11 +70,11 @@ uint64_t params_fingerprint(const diffus_params *p)
 }
 
 struct PlanSizes {
-    int64_t off[11];
+    int64_t off[12];
     int64_t bytes;
 };
 
-PlanSizes plan_sizes(int P, int64_t total_rays, int64_t n_tiles, int64_t n_ftiles)
+PlanSizes plan_sizes(int P, int64_t total_rays, int64_t n_tiles, int64_t n_ftiles, int64_t n_spk)
 {
     PlanSizes z;
     int64_t o = (int64_t)align256(sizeof(PlanHeader));
@@ -93,6 +93,7 @@ PlanSizes plan_sizes(int P, int64_t total_rays, int64_t n_tiles, int64_t n_ftile
     put(8, sizeof(int64_t) * total_rays);
     put(9, sizeof(BlurTile) * n_tiles);
     put(10, sizeof(TileDesc) * n_ftiles);
+    put(11, sizeof(SpkItem) * n_spk);
     z.bytes = o;
     return z;
 }
@@ -109,6 +110,15 @@ int64_t count_ftiles(const diffus_fan *fans, int P)
 {
     int64_t t = 0;
     for (int p = 0; p < P; p++) t += (int64_t)((fans[p].n_rays + kWarp - 1) / kWarp);
+    return t;
+}
+
+// Speckle work items: every tile's rows in blocks of kSpkRows.
+int64_t count_spk(const diffus_fan *fans, int P)
+{
+    int64_t t = 0;
+    for (int p = 0; p < P; p++)
+        t += (int64_t)((fans[p].n_rays + kWarp - 1) / kWarp) * ((fans[p].n_samples + kSpkRows - 1) / kSpkRows);
     return t;
 }
 
@@ -138,6 +148,9 @@ BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc
     L.frames = c.take<PoseFrame>((size_t)H.P);
     L.counter = c.take<unsigned>(8);
     L.y = blur ? c.take<float>((size_t)H.total_img) : nullptr;
+    // the one-warp-per-ray forward reads speckle factors drawn ahead of it
+    const bool spk_ahead = speckle && H.fwd_form == 1;
+    L.mbuf = spk_ahead ? c.take<float>((size_t)H.total_img) : nullptr;
     L.sel = RefineSel{nullptr, nullptr, nullptr, nullptr};
     if (refine) {
         L.sel.rinfo = c.take<int2>((size_t)H.total_rays);
@@ -149,7 +162,7 @@ BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc
     }
     L.fwd_bytes = c.used;
     L.gy = (blur || atten) ? c.take<float>((size_t)H.total_img) : nullptr;
-    L.mbuf = speckle ? c.take<float>((size_t)H.total_img) : nullptr;
+    if (!spk_ahead) L.mbuf = speckle ? c.take<float>((size_t)H.total_img) : nullptr;
     L.kbuf = c.take<float2>((size_t)H.total_gz);
     L.gz = c.take<float>((size_t)H.total_gz);
     L.part = c.take<double>(6 * (size_t)H.total_rays);
@@ -198,7 +211,7 @@ __global__ void __launch_bounds__(WARPS * 32, kFwdThreadsPerSM / (WARPS * 32)) k
                                                           int *__restrict__ valid, uint32_t *__restrict__ status,
                                                           unsigned *__restrict__ counter, float4 *__restrict__ ckpt,
                                                           float *__restrict__ mbuf, float2 *__restrict__ kbuf,
-                                                          RefineSel sel)
+                                                          const float *__restrict__ spk_in, RefineSel sel)
 {
     __shared__ float buf[WARPS][kSegPad];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -214,9 +227,12 @@ __global__ void __launch_bounds__(WARPS * 32, kFwdThreadsPerSM / (WARPS * 32)) k
             Ap.a2 = B.pose[rg.pose].a2;
             Ap.a2d = B.pose[rg.pose].a2d;
         }
+        // with the speckle drawn ahead (spk_in) the march reads the factors
+        // instead of writing them
         RayOut o{out + B.row_off[r], valid ? valid + r : nullptr, status, ckpt ? ckpt + B.ck_off[r] : nullptr,
-                 mbuf ? mbuf + B.row_off[r] : nullptr, kbuf ? kbuf + B.gz_off[r] : nullptr,
-                 sel.rinfo ? sel.rinfo + r : nullptr, sel.rlist, sel.rcount, r};
+                 (mbuf && !spk_in) ? mbuf + B.row_off[r] : nullptr, kbuf ? kbuf + B.gz_off[r] : nullptr,
+                 spk_in ? spk_in + B.row_off[r] : nullptr, sel.rinfo ? sel.rinfo + r : nullptr, sel.rlist,
+                 sel.rcount, r};
         march_fwd_ray<T, false, true>(vol, Ap, rg, o, buf[w]);
         __syncwarp();
     }
@@ -273,6 +289,21 @@ __global__ void __launch_bounds__(kTileWarpsBwd * 32, kBwdValThreadsPerSM / (kTi
     }
 }
 
+// Speckle factors of the whole batch ahead of the one-warp-per-ray forward:
+// one warp per (tile, 64-row block) item.
+__global__ void __launch_bounds__(kTileWarps * 32) k_batch_speckle(Speckle sp, const TileDesc *__restrict__ tiles,
+                                                                   const SpkItem *__restrict__ items, int64_t n_items,
+                                                                   float *__restrict__ mbuf)
+{
+    __shared__ SpkSmem sm[kTileWarps];
+    const int w = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * kTileWarps;
+    for (int64_t q = (int64_t)blockIdx.x * kTileWarps + w; q < n_items; q += nw) {
+        const SpkItem it = items[q];
+        speckle_item(sp, tiles[it.tile], it.k0, mbuf, sm[w]);
+    }
+}
+
 // Refined pass of the batch over the rays the FP32 pass listed (in the order
 // it listed them, which follows its longest-first queue).
 template <typename T, int WARPS>
@@ -302,7 +333,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_refine(const T *__restr
         }
         const FanDev fd{pp.n_rays, pp.S, pp.fov, pp.depth};
         RayOut o{out + B.row_off[r], valid ? valid + r : nullptr, status, ckpt ? ckpt + B.ck_off[r] : nullptr,
-                 nullptr, nullptr, nullptr, nullptr, nullptr, r};
+                 nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, r};
         refine_ray<T, true>(vol, Ap, rg, frames[rg.pose], fd, vp, o, sel.rinfo[r], buf[w], dbuf[w]);
         __syncwarp();
     }
@@ -406,6 +437,7 @@ struct FwdLaunch {
     int grid, form;
     const TileDesc *tiles;
     int64_t n_tiles;
+    const float *spk_in;   // speckle factors drawn ahead (one warp per ray only), or null
 };
 
 template <typename T, int WARPS>
@@ -419,7 +451,7 @@ void launch_fwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const 
                                                                  kp.kbuf, kp.bcar, sel);
     else
         k_batch_fwd<T, WARPS><<<fl.grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status, counter,
-                                                             kp.ckpt, kp.mbuf, kp.kbuf, sel);
+                                                             kp.ckpt, kp.mbuf, kp.kbuf, fl.spk_in, sel);
     if (sel.rinfo)
         k_batch_refine<T, WARPS><<<2 * sm_count(), WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, frames, vp, out, valid,
                                                                   status, kp.ckpt, sel);
@@ -498,7 +530,7 @@ extern "C" size_t diffus_batch_plan_bytes(const diffus_fan *fans, int32_t P)
         total_rays += fans[p].n_rays;
     }
     if (total_rays > INT32_MAX) return 0;
-    return (size_t)plan_sizes(P, total_rays, count_tiles(fans, P), count_ftiles(fans, P)).bytes;
+    return (size_t)plan_sizes(P, total_rays, count_tiles(fans, P), count_ftiles(fans, P), count_spk(fans, P)).bytes;
 }
 
 extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan *fans, int32_t P,
@@ -524,8 +556,8 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
         max_depth = std::max(max_depth, fans[p].depth_mm);
     }
     if (total_rays > INT32_MAX) return DIFFUS_E_DIMS;
-    const int64_t n_tiles = count_tiles(fans, P), n_ftiles = count_ftiles(fans, P);
-    PlanSizes z = plan_sizes(P, total_rays, n_tiles, n_ftiles);
+    const int64_t n_tiles = count_tiles(fans, P), n_ftiles = count_ftiles(fans, P), n_spk = count_spk(fans, P);
+    PlanSizes z = plan_sizes(P, total_rays, n_tiles, n_ftiles, n_spk);
     if (plan_bytes < (size_t)z.bytes) return DIFFUS_E_WORKSPACE;
 
     diffus_schedule sc = sched ? *sched : diffus_schedule{0, 0, 0, 0};
@@ -546,6 +578,7 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     H.total_ckpt = total_ck;
     H.n_tiles = n_tiles;
     H.n_ftiles = n_ftiles;
+    H.n_spk = n_spk;
     {
         int64_t tb = 0;
         for (int p = 0; p < P; p++)
@@ -561,7 +594,7 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     H.fwd_form = sc.fwd_form;
     H.off_pose = z.off[0]; H.off_depth = z.off[1]; H.off_ray0 = z.off[2]; H.off_ray_pose = z.off[3];
     H.off_ray_j = z.off[4]; H.off_order = z.off[5]; H.off_row_off = z.off[6]; H.off_gz_off = z.off[7];
-    H.off_ck_off = z.off[8]; H.off_tiles = z.off[9]; H.off_ftiles = z.off[10];
+    H.off_ck_off = z.off[8]; H.off_tiles = z.off[9]; H.off_ftiles = z.off[10]; H.off_spk = z.off[11];
     H.bytes = z.bytes;
     H.params_fp = params_fingerprint(prm);
 
@@ -619,6 +652,12 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     std::copy(ord.begin(), ord.end(), order);
     // forward tiles longest first (ties in plan order)
     std::stable_sort(ftiles, ftiles + n_ftiles, [](const TileDesc &x, const TileDesc &y) { return x.S > y.S; });
+    {
+        SpkItem *items = at_mut<SpkItem>(plan_host, H.off_spk);
+        int64_t q = 0;
+        for (int64_t tix = 0; tix < n_ftiles; tix++)
+            for (int k0 = 0; k0 < ftiles[tix].S; k0 += kSpkRows) items[q++] = SpkItem{(int32_t)tix, k0};
+    }
     // blur strips of the widest poses first (a strip's work grows with n_rays)
     std::stable_sort(tiles, tiles + n_tiles, [](const BlurTile &x, const BlurTile &y) { return x.n_rays > y.n_rays; });
 
@@ -689,7 +728,14 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     const FwdKeep kp{bwd ? L.ckpt : nullptr, bwd ? L.mbuf : nullptr, keep_samples ? L.kbuf : nullptr,
                      keep_samples ? L.bcar : nullptr};
     const VolPlace vp = make_place(vd);
-    FwdLaunch fl{grid, H.fwd_form, at<TileDesc>(plan_dev, H.off_ftiles), H.n_ftiles};
+    FwdLaunch fl{grid, H.fwd_form, at<TileDesc>(plan_dev, H.off_ftiles), H.n_ftiles, nullptr};
+    if (H.fwd_form == 1 && prm->speckle) {
+        // the speckle field first; the march reads it, and so does the adjoint
+        const int sgrid = (int)std::min<int64_t>((H.n_spk + kTileWarps - 1) / kTileWarps, (int64_t)sm_count() * 16);
+        k_batch_speckle<<<sgrid, kTileWarps * 32, 0, s>>>(A.sp, fl.tiles, at<SpkItem>(plan_dev, H.off_spk), H.n_spk,
+                                                          L.mbuf);
+        fl.spk_in = L.mbuf;
+    }
     if (H.fwd_form == 0) fl.grid = sm_count() * std::max(1, H.ctas_per_sm * H.warps / kTileWarps);
     if (vd->dtype == DIFFUS_F32)
         rc = launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0, kp, fl,

@@ -266,6 +266,11 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
     int kc = 0;                   // index along the ray of the next sample
     float(*pz)[32] = sm.pose[POSE ? w : 0];
     uint32_t next = q0;           // next unassigned run (warp-uniform)
+    // the first samples of the lane's next cell, loaded while the current
+    // cell's corner sums and flush run (the cell's other samples are loaded
+    // in its moment loop)
+    constexpr int kPre = 4;
+    float pre_g[kPre] = {0.0f, 0.0f, 0.0f, 0.0f};
     // lane i holds the index of run next + i, loaded one refill ahead
     uint32_t pre = next + lane < q1 ? order[next + lane] : 0u;
     for (;;) {
@@ -285,6 +290,8 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
                 dZ = run.dZ;
                 g = gzbuf + run.g_off;
                 left = run.len;
+#pragma unroll
+                for (int q = 0; q < kPre; q++) pre_g[q] = q < left ? __ldg(g + q) : 0.0f;
                 cx = cy = cz = 0;
                 if (POSE) {
                     slot = idx;
@@ -313,19 +320,21 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
         // moments of dL/dZ over the cell's samples
         float M0 = 0.0f, M1 = 0.0f, M2 = 0.0f, M3 = 0.0f;
         const int kmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+        auto moment = [&](float gk, int k) {
+            const float kf = (float)k;
+            M0 += gk;
+            float t = gk * kf;
+            M1 += t;
+            t *= kf;
+            M2 += t;
+            M3 = fmaf(t, kf, M3);
+        };
+#pragma unroll
+        for (int k = 0; k < kPre; k++)
+            if (k < len) moment(pre_g[k], k);
 #pragma unroll 4
-        for (int k = 0; k < kmax; k++) {
-            if (k < len) {
-                const float gk = __ldg(g + k);
-                const float kf = (float)k;
-                M0 += gk;
-                float t = gk * kf;
-                M1 += t;
-                t *= kf;
-                M2 += t;
-                M3 = fmaf(t, kf, M3);
-            }
-        }
+        for (int k = kPre; k < kmax; k++)
+            if (k < len) moment(__ldg(g + k), k);
         // corner sums: yz products as quadratics in k, then the x factors
         float v[8];
         {
@@ -379,6 +388,8 @@ __device__ __forceinline__ void gather_runs(const Run *__restrict__ runs, const 
             Z += (long long)len * dZ;
             g += len;
             left -= len;
+#pragma unroll
+            for (int q = 0; q < kPre; q++) pre_g[q] = q < left ? __ldg(g + q) : 0.0f;
             cx -= len;
             cy -= len;
             cz -= len;

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kWarpsFwd * 32) k_march_fwd(const T *__restric
     const int j = blockIdx.x * kWarpsFwd + w;
     if (j >= n_rays) return;
     RayGeo rg = geo[j];
-    RayOut o{out + (size_t)j * rg.S, valid ? valid + j : nullptr, status, nullptr, nullptr, nullptr,
+    RayOut o{out + (size_t)j * rg.S, valid ? valid + j : nullptr, status, nullptr, nullptr, nullptr, nullptr,
              sel.rinfo ? sel.rinfo + j : nullptr, sel.rlist, sel.rcount, j};
     march_fwd_ray<T>(vol, A, rg, o, buf[w]);
 }
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kWarpsFwd * 32, 1) k_march_refine(const T *__r
         if (q >= n) break;
         const int j = sel.rlist[q];
         const RayGeo rg = geo[j];
-        RayOut o{out + (size_t)j * rg.S, valid ? valid + j : nullptr, status, nullptr, nullptr, nullptr,
+        RayOut o{out + (size_t)j * rg.S, valid ? valid + j : nullptr, status, nullptr, nullptr, nullptr, nullptr,
                  nullptr, nullptr, nullptr, j};
         refine_ray<T, false>(vol, A, rg, f, fan, vp, o, sel.rinfo[j], buf[w], dbuf[w]);
         __syncwarp();

@@ -55,6 +55,7 @@ struct RayOut {
     float4 *ckpt;     // nullable: scan carry (b0, b1, D) at every segment start, for the adjoint
     float *mrow;      // nullable: speckle factor of every row, for the adjoint
     float2 *krow;     // nullable: per sample k = 0..S, (zref + dz, r_{k-1}) for the adjoint (r_{-1} = 0)
+    const float *min; // nullable: the row's speckle factors, drawn ahead of the march (then not drawn here)
     // selective refinement (FP32 pass; all null when refinement is off):
     int2 *rinfo;      // this ray's (segments for the refined pass, first ill-posed depth of the FP32 pass)
     int *rlist;       // rays that need the refined pass are appended here ...
@@ -237,11 +238,19 @@ __device__ __forceinline__ void chunk_speckle(const Speckle &sp, int i0, int S, 
     uint4 gR = shfl_down_u4(gA, 1);
     if (lane == 0) gL = edge;
     if (lane == 31) gR = edge;
-    float nu[16];
-    nu[0] = ih_normal(gL.x); nu[1] = ih_normal(gL.y); nu[2] = ih_normal(gL.z); nu[3] = ih_normal(gL.w);
-    nu[4] = ih_normal(gA.x); nu[5] = ih_normal(gA.y); nu[6] = ih_normal(gA.z); nu[7] = ih_normal(gA.w);
-    nu[8] = ih_normal(gB.x); nu[9] = ih_normal(gB.y); nu[10] = ih_normal(gB.z); nu[11] = ih_normal(gB.w);
-    nu[12] = ih_normal(gR.x); nu[13] = ih_normal(gR.y); nu[14] = ih_normal(gR.z); nu[15] = ih_normal(gR.w);
+    // byte sums of rows i0-4 .. i0+11; the radial normal of row i0+t is the
+    // window sum of entries t+4-L .. t+4+L, centred and scaled (integer sums
+    // are exact, so the window can move by one add and one subtract)
+    const int su[16] = {(int)__vsadu4(gL.x, 0u), (int)__vsadu4(gL.y, 0u), (int)__vsadu4(gL.z, 0u),
+                        (int)__vsadu4(gL.w, 0u), (int)__vsadu4(gA.x, 0u), (int)__vsadu4(gA.y, 0u),
+                        (int)__vsadu4(gA.z, 0u), (int)__vsadu4(gA.w, 0u), (int)__vsadu4(gB.x, 0u),
+                        (int)__vsadu4(gB.y, 0u), (int)__vsadu4(gB.z, 0u), (int)__vsadu4(gB.w, 0u),
+                        (int)__vsadu4(gR.x, 0u), (int)__vsadu4(gR.y, 0u), (int)__vsadu4(gR.z, 0u),
+                        (int)__vsadu4(gR.w, 0u)};
+    const int L = sp.Lr;
+    const bool full = L == 4;   // the default window moves by one add and one subtract
+    int Wf = su[0] + su[1] + su[2] + su[3] + su[4] + su[5] + su[6] + su[7] + su[8];
+    const int off_nr = (2 * L + 1) * 510;
     const int kb1 = (S + 3) / 4, kb2 = (2 * S + 3) / 4, kb3 = (3 * S + 3) / 4;
     const float invS = 1.0f / (float)S;
     uint32_t cur_grp = 0xffffffffu;
@@ -251,9 +260,14 @@ __device__ __forceinline__ void chunk_speckle(const Speckle &sp, int i0, int S, 
         const int i = i0 + t;
         m[t] = 1.0f;
         if (i < S) {
-            float nr = 0.0f;
+            int W = Wf;
+            if (!full) {
+                W = su[t + 4];
 #pragma unroll
-            for (int d = -4; d <= 4; d++) nr = fmaf(sp.wr[d + 4], nu[t + 4 + d], nr);
+                for (int d = 1; d <= 4; d++)
+                    if (d <= L) W += su[t + 4 - d] + su[t + 4 + d];
+            }
+            const float nr = (float)(W - off_nr) * sp.nr_scale;
             uint32_t cell = grain_cell(i, kb1, kb2, kb3, sp.gshift);
             uint32_t grp = cell >> 2;
             if (grp != cur_grp) {
@@ -263,6 +277,7 @@ __device__ __forceinline__ void chunk_speckle(const Speckle &sp, int i0, int S, 
             float ng = ih_normal(pick4(gw, cell & 3u));
             m[t] = speckle_factor(sp, (float)(i + 1) * invS, nr, ng);
         }
+        if (t + 1 < kChunk) Wf += su[t + 9] - su[t];
     }
 }
 
@@ -344,7 +359,10 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
             Ds *= dall;
         }
         float m[kChunk];
-        if (A.sp.on) {
+        if (!REFINE && out.min) {
+#pragma unroll
+            for (int t = 0; t < kChunk; t++) m[t] = (i0 + t < S) ? __ldcs(out.min + i0 + t) : 1.0f;
+        } else if (A.sp.on) {
             chunk_speckle(A.sp, i0, S, rg.ray, pose, m);
         } else {
 #pragma unroll

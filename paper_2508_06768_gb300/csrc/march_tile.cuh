@@ -212,3 +212,93 @@ __device__ void march_fwd_tile(const T *__restrict__ vol, const MarchArgs &A, co
 }
 
 }  // namespace dfs
+
+namespace dfs {
+
+// ------------------------------------------------ speckle field, ahead of the march
+
+constexpr int kSpkRows = 64;   // rows of one speckle work item
+constexpr int kSpkLd = kSpkRows + 1;
+
+// A speckle work item: rows k0 .. k0+63 of the rays of one forward tile.
+struct SpkItem {
+    int32_t tile, k0;
+};
+
+struct SpkSmem {
+    float m[kWarp * kSpkLd];
+    float zr[kSpkRows], zg[kSpkRows];
+};
+
+// Speckle factors (Section 2.4) of rows k0 .. k0+63 of the tile's rays,
+// written to mbuf at the rays' image offsets.  The factors depend only on the
+// seed, the pose and ray indices, the row and S, never on the volume, so they
+// can be drawn before the march and read by it.  A lane runs its ray's rows
+// in order: the radial window from byte sums of Philox groups of four rows
+// (exact integer sums, as the march's own speckle), one grain normal per
+// grain cell, and the same factor arithmetic, so the factors equal the
+// march's bit for bit.
+__device__ void speckle_item(const Speckle &sp, const TileDesc &tl, int k0, float *__restrict__ mbuf, SpkSmem &sm)
+{
+    const int lane = threadIdx.x & 31;
+    const int S = tl.S, cnt = tl.cnt;
+    const uint32_t pose = sp.pose_ctr + (uint32_t)tl.pose;
+    const uint32_t ray = (uint32_t)(tl.j0 + lane);
+    const int n = min(kSpkRows, S - k0);
+    const float invS = 1.0f / (float)S;
+    for (int e = lane; e < kSpkRows; e += kWarp) {
+        const float lz = __log2f((float)(k0 + e + 1) * invS);
+        sm.zr[e] = sp.Ar * exp2f(sp.pr * lz);
+        sm.zg[e] = sp.Ag * exp2f(sp.pg * lz);
+    }
+    int sm1[4], s0[4];
+    group_sums(radial_group(sp, (k0 >> 2) - 1, (int)ray, pose), sm1);
+    group_sums(radial_group(sp, k0 >> 2, (int)ray, pose), s0);
+    const int L = sp.Lr, off_nr = (2 * L + 1) * 510;
+    const int kb1 = (S + 3) / 4, kb2 = (2 * S + 3) / 4, kb3 = (3 * S + 3) / 4;
+    uint32_t cur_grp = 0xffffffffu;
+    uint4 gw = make_uint4(0, 0, 0, 0);
+    __syncwarp();
+    for (int g4 = 0; g4 < kSpkRows / 4; g4++) {
+        const int q = (k0 >> 2) + g4;
+        if (4 * q >= k0 + n) break;
+        int sp1[4];
+        group_sums(radial_group(sp, q + 1, (int)ray, pose), sp1);
+        const int w9[12] = {sm1[0], sm1[1], sm1[2], sm1[3], s0[0], s0[1], s0[2], s0[3],
+                            sp1[0], sp1[1], sp1[2], sp1[3]};
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const int i = 4 * q + t;
+            if (i >= k0 + n) break;
+            int W = w9[t + 4];
+#pragma unroll
+            for (int d = 1; d <= 4; d++)
+                if (d <= L) W += w9[t + 4 - d] + w9[t + 4 + d];
+            const float nr = (float)(W - off_nr) * sp.nr_scale;
+            const int b = (i >= kb1) + (i >= kb2) + (i >= kb3);
+            const int kbb = b == 0 ? 0 : (b == 1 ? kb1 : (b == 2 ? kb2 : kb3));
+            const uint32_t cell = ((uint32_t)b << 24) | (uint32_t)((i - kbb) >> (sp.gshift + b));
+            if ((cell >> 2) != cur_grp) {   // the same row for every lane
+                cur_grp = cell >> 2;
+                gw = philox10_rk(make_uint4(cur_grp, ray, pose, 1u), sp.rk);
+            }
+            const float ng = ih_normal(pick4(gw, cell & 3u));
+            const int e = i - k0;
+            sm.m[lane * kSpkLd + e] = fmaxf(fmaf(sm.zr[e], nr, fmaf(sm.zg[e], ng, 1.0f)), 0.0f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            sm1[u] = s0[u];
+            s0[u] = sp1[u];
+        }
+    }
+    __syncwarp();
+    // one ray's 64 rows per pair of store instructions
+    for (int rr = 0; rr < cnt; rr++) {
+        float *dst = mbuf + tl.row0 + (int64_t)rr * S + k0;
+        for (int e = lane; e < n; e += kWarp) __stcs(dst + e, sm.m[rr * kSpkLd + e]);
+    }
+    __syncwarp();
+}
+
+}  // namespace dfs
