@@ -142,9 +142,9 @@ BOUND = {"march_fwd": "alu", "march_bwd": "alu", "gather_units": "alu", "blur": 
 # speckle kernel plus the march), divided by its ray-samples); absent where
 # the kernel changed since.
 NCU_DRAM_PER_UNIT = {"blur": 6.12, "blur_T": 6.13, "gather_units": 7.44}
-# the marches' figures depend on the forward form (fwd_form 1: one warp per
-# ray; 0: one lane per ray), set from the capture of that form
-NCU_DRAM_PER_UNIT_FORM = {1: {"march_fwd": 18.81, "march_bwd": 19.71}, 0: {"march_fwd": 25.71, "march_bwd": 21.52}}
+# the marches' figures depend on the forward form (fwd_form 0: one warp per
+# ray; 1: one lane per ray), set from the capture of that form
+NCU_DRAM_PER_UNIT_FORM = {0: {"march_fwd": 18.81, "march_bwd": 19.71}, 1: {"march_fwd": 25.71, "march_bwd": 21.52}}
 
 
 def median_pose_order(fans):
@@ -676,10 +676,10 @@ def run_native(args):
         sched = B.ScheduleDesc(w, c, g, f)
     elif not args.no_autotune:
         # (warps per CTA, CTAs per SM, gather CTAs per SM, forward form):
-        # form 0 runs the marches with one lane per ray (grids of 4-warp CTAs
-        # sized from warps x CTAs), form 1 with one warp per ray
+        # form 0 runs the marches with one warp per ray, form 1 with one lane
+        # per ray (grids of 4-warp CTAs sized from warps x CTAs)
         sched, _ = autotune(vol_d, vol.spacing, vol.origin, fans, prm, poses_d, G,
-                            candidates=[(4, 3, 8, 0), (4, 4, 8, 0), (4, 4, 16, 0), (4, 6, 8, 0), (8, 3, 8, 1)],
+                            candidates=[(8, 3, 8, 0), (8, 2, 8, 0), (8, 3, 16, 0), (4, 6, 8, 0), (4, 3, 8, 1)],
                             reps=1)
     r = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm, schedule=sched, with_bwd=True, pose_ctr=pose0)
 
@@ -826,7 +826,7 @@ def run_native(args):
     timed = {k: v for k, v in kern_ms.items() if k in BOUND}
     dom = max(timed, key=timed.get)
     t_dom = kern_ms[dom] * 1e-3
-    form = 1 if sched is None else int(sched.fwd_form)
+    form = 0 if sched is None else int(sched.fwd_form)
     dram = NCU_DRAM_PER_UNIT_FORM[form].get(dom, NCU_DRAM_PER_UNIT.get(dom))
     if BOUND[dom] == "alu":
         ach = ALGO_OPS[dom] * total / t_dom / 1e12
@@ -860,7 +860,8 @@ def run_native(args):
         cpu, err = cpu_leg(vol, poses, fans, prm, images=images_h, grad_poses=gposes_h,
                            G=G.cpu().numpy(), offsets=r.offsets)
 
-    # kernels per step: pose frames, ray setup, forward march, [blur, blur
+    # kernels per step: pose frames, ray setup, [speckle field, with the
+    # warp-per-ray form], forward march, [refined pass], [blur, blur
     # transpose] or [two depth-gain row passes], adjoint march, pose
     # reduction; gather: brick runs, one radix pass per 8 bits of brick id of
     # (histogram, 3 scan kernels, scatter), brick bounds, unit counts, 3 scan
@@ -868,7 +869,9 @@ def run_native(args):
     # gather, voxel reduction, per-ray pose terms (memsets are not kernels)
     nbricks = int(np.prod([(n - 2) // 8 + 1 for n in vol.data.shape]))
     passes = (nbricks.bit_length() + 7) // 8
-    launches = (5 + (2 if prm.blur else (2 if prm.atten else 0)) +
+    form = 0 if sched is None else sched.fwd_form
+    launches = (5 + (1 if form == 0 and prm.speckle else 0) + (1 if prm.refine else 0) +
+                (2 if prm.blur else (2 if prm.atten else 0)) +
                 (1 + 5 * passes + 1 + 1 + 3 + 1 + 3 + 1 + 1 + 1))
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -205,10 +205,11 @@ int diffus_render_fwd_noalloc(const void *vol, const diffus_volume_desc *vd, con
 /* Launch schedule of the batched path.  rays_per_cta: warps (one ray each)
  * per CTA of the persistent marches (2, 4 or 8); ctas_per_sm: resident CTAs
  * per SM used to size the persistent march grids; brick: CTAs per SM of the
- * volume-gradient gather grid (1..64); fwd_form: how the forward march maps
- * rays to lanes, 0 (default) one lane per ray over tiles of 32 consecutive
- * rays of a pose (the rays' depth recurrences run side by side), 1 one warp
- * per ray (lanes along the depth, combined by a warp scan).  Zero fields of
+ * volume-gradient gather grid (1..64); fwd_form: how the marches map rays
+ * to lanes, 0 (default) one warp per ray (lanes along the depth, combined by
+ * a warp scan; the speckle factors are drawn by a kernel of their own ahead
+ * of the march), 1 one lane per ray over tiles of 32 consecutive rays of a
+ * pose (the rays' depth recurrences run side by side).  Zero fields of
  * the first three take defaults (4, 4, 8).  rays_per_cta, ctas_per_sm and
  * brick change launch shapes only, never the arithmetic of a ray or a
  * brick; the two forward forms order the FP32 arithmetic of a ray

@@ -149,7 +149,7 @@ BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc
     L.counter = c.take<unsigned>(8);
     L.y = blur ? c.take<float>((size_t)H.total_img) : nullptr;
     // the one-warp-per-ray forward reads speckle factors drawn ahead of it
-    const bool spk_ahead = speckle && H.fwd_form == 1;
+    const bool spk_ahead = speckle && H.fwd_form == 0;
     L.mbuf = spk_ahead ? c.take<float>((size_t)H.total_img) : nullptr;
     L.sel = RefineSel{nullptr, nullptr, nullptr, nullptr};
     if (refine) {
@@ -167,7 +167,7 @@ BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc
     L.gz = c.take<float>((size_t)H.total_gz);
     L.part = c.take<double>(6 * (size_t)H.total_rays);
     L.ckpt = c.take<float4>((size_t)H.total_ckpt);
-    L.bcar = H.fwd_form == 0 ? c.take<float4>((size_t)H.total_bcar) : nullptr;
+    L.bcar = H.fwd_form == 1 ? c.take<float4>((size_t)H.total_bcar) : nullptr;
     L.gather_ws = (void *)c.take<char>(gather_workspace_bytes(vd, H.total_rays, H.max_depth));
     L.bytes = c.used;
     return L;
@@ -431,8 +431,8 @@ int sm_count()
     return sms;
 }
 
-// The forward's launch: fwd_form 0 marches tiles with one lane per ray
-// (grid = CTAs per SM x SMs of kTileWarps warps), 1 one warp per ray.
+// The forward's launch: fwd_form 0 one warp per ray, 1 tiles with one lane
+// per ray (grid = CTAs per SM x SMs of kTileWarps warps).
 struct FwdLaunch {
     int grid, form;
     const TileDesc *tiles;
@@ -445,7 +445,7 @@ void launch_fwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const 
                   uint32_t *status, unsigned *counter, const FwdKeep &kp, const FwdLaunch &fl, const RefineSel &sel,
                   const PoseFrame *frames, const VolPlace &vp, cudaStream_t s)
 {
-    if (fl.form == 0)
+    if (fl.form == 1)
         k_batch_fwd_tiles<T><<<fl.grid, kTileWarps * 32, 0, s>>>((const T *)vol, A, B, geo, fl.tiles, fl.n_tiles,
                                                                  out, valid, status, counter, kp.ckpt, kp.mbuf,
                                                                  kp.kbuf, kp.bcar, sel);
@@ -729,14 +729,14 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
                      keep_samples ? L.bcar : nullptr};
     const VolPlace vp = make_place(vd);
     FwdLaunch fl{grid, H.fwd_form, at<TileDesc>(plan_dev, H.off_ftiles), H.n_ftiles, nullptr};
-    if (H.fwd_form == 1 && prm->speckle) {
+    if (H.fwd_form == 0 && prm->speckle) {
         // the speckle field first; the march reads it, and so does the adjoint
         const int sgrid = (int)std::min<int64_t>((H.n_spk + kTileWarps - 1) / kTileWarps, (int64_t)sm_count() * 16);
         k_batch_speckle<<<sgrid, kTileWarps * 32, 0, s>>>(A.sp, fl.tiles, at<SpkItem>(plan_dev, H.off_spk), H.n_spk,
                                                           L.mbuf);
         fl.spk_in = L.mbuf;
     }
-    if (H.fwd_form == 0) fl.grid = sm_count() * std::max(1, H.ctas_per_sm * H.warps / kTileWarps);
+    if (H.fwd_form == 1) fl.grid = sm_count() * std::max(1, H.ctas_per_sm * H.warps / kTileWarps);
     if (vd->dtype == DIFFUS_F32)
         rc = launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0, kp, fl,
                                  L.sel, L.frames, vp, s);
@@ -775,7 +775,7 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     mark(DIFFUS_TR_MARCH_BWD);
     // with a volume gradient the gather also forms the pose terms, so the
     // adjoint march reads the kept samples (march_pose above)
-    if (H.fwd_form == 0 && !march_pose) {
+    if (H.fwd_form == 1 && !march_pose) {
         // six 2-warp CTAs (two input stages each) fill an SM's shared memory
         const int bgrid = sm_count() * 6;
         k_batch_bwd_tiles<<<bgrid, kTileWarpsBwd * 32, 0, s>>>(A, B, at<TileDesc>(plan_dev, H.off_ftiles), H.n_ftiles, gy,

@@ -62,12 +62,6 @@ class BatchRenderer:
         self.pose_ctr = pose_ctr
         self.schedule = schedule
         dev = volume.device
-        if schedule is None:
-            # measured on the 512-pose batch: one lane per ray is the faster
-            # forward alone (2.16 against 2.64 ms), one warp per ray the
-            # faster forward+backward (6.39 against 6.82 ms)
-            schedule = B.ScheduleDesc(0, 0, 0, 1 if with_bwd else 0)
-            self.schedule = schedule
         plan, offs, wsf, wsb = B.batch_plan(self.volume, spacing, origin, self.fans, params, schedule)
         self.plan_host = plan.pin_memory() if torch.cuda.is_available() else plan
         self.plan_dev = plan.to(dev)

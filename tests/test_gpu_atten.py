@@ -45,7 +45,7 @@ def test_depth_gain_batch_equals_single_pose():
     prm = I.Params(seed=41, mode=1, atten=1)
     v = torch.from_numpy(vol.data).cuda()
     # the single-pose path's forward form (one warp per ray): bitwise
-    r = BatchRenderer(v, vol.spacing, vol.origin, fans, prm, with_bwd=True, schedule=B.ScheduleDesc(0, 0, 0, 1))
+    r = BatchRenderer(v, vol.spacing, vol.origin, fans, prm, with_bwd=True, schedule=B.ScheduleDesc(0, 0, 0, 0))
     Gs = [I.random_weights((f.n_rays, f.n_samples), 70 + p) for p, f in enumerate(fans)]
     r.run(torch.from_numpy(poses).cuda(), torch.from_numpy(np.concatenate([g.ravel() for g in Gs])).cuda())
     torch.cuda.synchronize()

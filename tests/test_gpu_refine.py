@@ -112,8 +112,8 @@ def test_refine_batch_equals_single_pose():
     fans = I.random_batch_fans(4, seed=31, rays=(5, 30), samples=(100, 900), ds_mm=0.05, fov_deg=40.0)
     prm = I.Params(seed=31, mode=0, refine=1)
     v = torch.from_numpy(vol.data).cuda()
-    for form in (1, 0):
-        # form 1 runs the single-pose path's FP32 pass: bitwise; form 0's FP32
+    for form in (0, 1):
+        # form 0 runs the single-pose path's FP32 pass: bitwise; form 1's FP32
         # pass orders the arithmetic differently, so rows outside the refined
         # ranges agree to rounding (and the refined ranges, redone by the same
         # refined pass from the same samples, agree to rounding as well)
@@ -127,7 +127,7 @@ def test_refine_batch_equals_single_pose():
             ofs = sum(g.n_rays for g in fans[:p])
             assert np.array_equal(r.ray_valid[ofs:ofs + f.n_rays].cpu().numpy(), valid.cpu().numpy())
             a, b = r.image(p).cpu().numpy(), img.cpu().numpy()
-            if form == 1:
+            if form == 0:
                 assert np.array_equal(a, b)
             else:
                 good = np.arange(f.n_samples)[None, :] < np.minimum(valid.cpu().numpy(), f.n_samples)[:, None]
