@@ -137,14 +137,13 @@ ALGO_BYTES = {"march_fwd": 4.0, "blur": 8.0, "blur_T": 8.0, "march_bwd": 8.0, "g
 ALGO_OPS = {"march_fwd": 111.0, "march_bwd": 77.0, "gather_units": 45.0}
 BOUND = {"march_fwd": "alu", "march_bwd": "alu", "gather_units": "alu", "blur": "hbm", "blur_T": "hbm"}
 # DRAM bytes per ray-sample measured by ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch over a prefix of the workload (blurs
-# and gather: 64 poses; marches: 192 poses, the forward phase being the
-# speckle kernel plus the march), divided by its ray-samples); absent where
-# the kernel changed since.
-NCU_DRAM_PER_UNIT = {"blur": 6.12, "blur_T": 6.13, "gather_units": 7.44}
+# dram__bytes_write.sum of one launch over the first 192 poses of the
+# workload, the forward phase being the speckle kernel plus the march,
+# divided by its ray-samples); absent where the kernel changed since.
+NCU_DRAM_PER_UNIT = {"blur": 8.01, "blur_T": 7.84, "gather_units": 8.57}
 # the marches' figures depend on the forward form (fwd_form 0: one warp per
 # ray; 1: one lane per ray), set from the capture of that form
-NCU_DRAM_PER_UNIT_FORM = {0: {"march_fwd": 18.81, "march_bwd": 19.71}, 1: {"march_fwd": 25.71, "march_bwd": 21.52}}
+NCU_DRAM_PER_UNIT_FORM = {0: {"march_fwd": 18.83, "march_bwd": 19.68}, 1: {}}
 
 
 def median_pose_order(fans):
@@ -546,14 +545,22 @@ def run_configs(torch, B, flush, stream, steps, warmup, with_cpu=True):
         torch.cuda.synchronize()
         return ms, img.cpu().numpy().astype(np.float64), valid.cpu().numpy()
 
+    def per_call(f, min_s=0.5):
+        # repeated until min_s has passed, so that a small render is not
+        # timed on one call's thread start-up
+        f()
+        n, t0 = 0, time.perf_counter()
+        while True:
+            f()
+            n += 1
+            t = time.perf_counter() - t0
+            if t >= min_s:
+                return t / n
+
     def cpu_times(vol, pose, fan, prm, rays=None):
         import cpu_baseline
-        t0 = time.perf_counter()
-        oracle.render(vol, pose, fan, prm, rays=rays)
-        t_def = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        cpu_baseline.render(vol, pose, fan, prm)
-        t_rec = time.perf_counter() - t0
+        t_def = per_call(lambda: oracle.render(vol, pose, fan, prm, rays=rays))
+        t_rec = per_call(lambda: cpu_baseline.render(vol, pose, fan, prm))
         nr = fan.n_rays if rays is None else len(rays)
         return {"definition_route": nr * fan.n_samples / t_def, "recurrence_route": fan.n_rays * fan.n_samples / t_rec,
                 "cores": oracle.num_threads(), "unit": UNIT,
@@ -739,12 +746,19 @@ def run_native(args):
 
     # ---- end to end through the public API: host buffers, copies inside the timed region.
     # The step pipelines its transfers the way a user of the API can: the
-    # volume and poses go up first, dL/dimage goes up on a second stream while
-    # the forward marches (the call waits on its event before the backward),
-    # and the images come down on a third stream from the forward's end event
-    # while the backward runs; the gradients come down last.
+    # volume and poses go up first, dL/dimage goes up on a second stream in
+    # the plan's backward chunks while the forward marches (each chunk's event
+    # releases that chunk's blur transpose and adjoint march), and the images
+    # come down on a third stream from the forward's end event while the
+    # backward runs; the gradients come down last.
     e2e = None
     if not args.no_e2e:
+        n_chunks = 4   # measured: 4 ranges 6.85 ms, 8 ranges 7.14, one 7.53 (each range's launches end on a tail)
+        s5 = sched if sched is not None else B.ScheduleDesc(0, 0, 0, 0)
+        r_e2e = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm, with_bwd=True, pose_ctr=pose0,
+                              schedule=B.ScheduleDesc(s5.rays_per_cta, s5.ctas_per_sm, s5.brick, s5.fwd_form,
+                                                      n_chunks))
+        ranges = r_e2e.chunk_ranges()
         vol_h = torch.from_numpy(vol.data).pin_memory()
         poses_h = torch.from_numpy(poses).pin_memory()
         G_h = G.cpu().pin_memory()
@@ -754,13 +768,21 @@ def run_native(args):
         h2d = vol_h.numel() * 4 + poses_h.numel() * 4 + G_h.numel() * 4
         d2h = img_h.numel() * 4 + gv_h.numel() * 4 + gp_h.numel() * 4
         up, down = torch.cuda.Stream(), torch.cuda.Stream()
-        ev_fwd_end, ev_g = torch.cuda.Event(), torch.cuda.Event()
+        ev_fwd_end = torch.cuda.Event()
+        ev_g = [torch.cuda.Event() for _ in ranges]
         ev_fwd_end.record(stream)
-        ev_g.record(stream)          # torch creates the underlying events lazily
+        for e in ev_g:
+            e.record(stream)          # torch creates the underlying events lazily
         tr = B.TraceDesc()
         tr.event[3] = ev_fwd_end.cuda_event      # DIFFUS_TR_FWD_END
-        tr.wait_before_bwd = ev_g.cuda_event
-        tt = 0.0
+        for c, e in enumerate(ev_g):
+            tr.wait_chunk[c] = e.cuda_event
+
+        def exchange_e2e():
+            if sharded:
+                allreduce_volume_grad(r_e2e.grad_vol)
+
+        step_ms = []
         n_e2e = max(1, min(args.steps, 10))
         for it in range(n_e2e + 1):
             flush.zero_()
@@ -769,22 +791,23 @@ def run_native(args):
             poses_d.copy_(poses_h, non_blocking=True)
             up.wait_stream(stream)
             with torch.cuda.stream(up):
-                G.copy_(G_h, non_blocking=True)
-                ev_g.record(up)
-            r.run(poses_d, G, stream=stream, trace=tr)
+                for (a, b), e in zip(ranges, ev_g):
+                    G[a:b].copy_(G_h[a:b], non_blocking=True)
+                    e.record(up)
+            r_e2e.run(poses_d, G, stream=stream, trace=tr)
             down.wait_event(ev_fwd_end)
             with torch.cuda.stream(down):
-                img_h.copy_(r.images, non_blocking=True)
-            exchange()
-            gv_h.copy_(r.grad_vol, non_blocking=True)
-            gp_h.copy_(r.grad_poses, non_blocking=True)
+                img_h.copy_(r_e2e.images, non_blocking=True)
+            exchange_e2e()
+            gv_h.copy_(r_e2e.grad_vol, non_blocking=True)
+            gp_h.copy_(r_e2e.grad_poses, non_blocking=True)
             stream.wait_stream(down)
             stream.wait_stream(up)
             e1.record(stream)
             torch.cuda.synchronize()
             if it > 0:
-                tt += e0.elapsed_time(e1)
-        e2e_ms = tt / n_e2e
+                step_ms.append(e0.elapsed_time(e1))
+        e2e_ms = float(np.mean(step_ms))
         if ws > 1:
             t = torch.tensor([e2e_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -804,8 +827,12 @@ def run_native(args):
         del probe_h, probe_d
         e2e = {"value": job_units / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
-               "form": "one diffus_render_batch call per step; uploads and downloads overlap the marches",
+               "ms_min_median_max": [float(np.min(step_ms)), float(np.median(step_ms)), float(np.max(step_ms))],
+               "form": "one diffus_render_batch call per step; dL/dimage uploaded in %d pose ranges, each "
+                       "releasing its blur transpose and adjoint march; images downloaded while the backward "
+                       "runs" % len(ranges),
                "link": link}
+        del r_e2e
     clk.__exit__(None, None, None)
     clocks = clk.summary()
 

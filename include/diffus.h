@@ -210,15 +210,27 @@ int diffus_render_fwd_noalloc(const void *vol, const diffus_volume_desc *vd, con
  * a warp scan; the speckle factors are drawn by a kernel of their own ahead
  * of the march), 1 one lane per ray over tiles of 32 consecutive rays of a
  * pose (the rays' depth recurrences run side by side).  Zero fields of
- * the first three take defaults (4, 4, 8).  rays_per_cta, ctas_per_sm and
- * brick change launch shapes only, never the arithmetic of a ray or a
- * brick; the two forward forms order the FP32 arithmetic of a ray
- * differently, so their images agree to rounding, not bitwise. */
+ * the first three take defaults: 4 warps per CTA, as many CTAs per SM as
+ * fill 768 threads (the marches' register budget: 6 with 4 warps), and 8
+ * gather CTAs per SM.  bwd_chunks (0 or 1: one chunk; at most
+ * DIFFUS_MAX_BWD_CHUNKS): the poses are split into that many contiguous
+ * ranges of about equal work (diffus_batch_plan_chunks returns them), and
+ * the backward runs range by range (blur transpose, then adjoint march of
+ * the range's rays), each after its own wait event (diffus_trace.wait_chunk),
+ * so the backward can start on the first poses' dL/dimage while the rest is
+ * still being uploaded.  The forward-only one-lane-per-ray backward runs as
+ * one range after all events.  rays_per_cta, ctas_per_sm, brick and
+ * bwd_chunks change launch shapes and order only, never the arithmetic of a
+ * ray or a brick (results are bitwise the same); the two forward forms order
+ * the FP32 arithmetic of a ray differently, so their images agree to
+ * rounding, not bitwise. */
+#define DIFFUS_MAX_BWD_CHUNKS 16
 typedef struct {
     int32_t rays_per_cta;
     int32_t ctas_per_sm;
     int32_t brick;
     int32_t fwd_form;
+    int32_t bwd_chunks;
 } diffus_schedule;
 
 /* Optional tracing of the batched call: when non-NULL, the library records
@@ -247,6 +259,12 @@ typedef struct {
      * march; the forward's outputs can likewise be downloaded from the
      * DIFFUS_TR_FWD_END event on while the backward runs. */
     void *wait_before_bwd;
+    /* Optional inputs of a plan with bwd_chunks > 1: the stream waits on
+     * wait_chunk[c] (a cudaEvent_t, or NULL) before the backward of pose
+     * range c, so a caller that uploads dL/dimage range by range records
+     * event c after range c's copy.  Entries at and past the plan's chunk
+     * count are ignored. */
+    void *wait_chunk[DIFFUS_MAX_BWD_CHUNKS];
 } diffus_trace;
 
 /* Size of the plan blob for P fans (host). */
@@ -263,6 +281,15 @@ size_t diffus_batch_plan_bytes(const diffus_fan *fans, int32_t P);
 int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan *fans, int32_t P,
                       const diffus_params *prm, const diffus_schedule *sched, void *plan_host,
                       size_t plan_bytes, int64_t *img_offsets, size_t *ws_fwd, size_t *ws_bwd);
+
+/* Pose ranges of the backward chunks of a plan (host): writes the first
+ * pose of each chunk and, last, P into first_pose (host int32[n + 1], n the
+ * chunk count) and returns n (>= 1), or a negative error code (DIFFUS_E_NULL,
+ * DIFFUS_E_PLAN for a buffer that is not a plan, DIFFUS_E_WORKSPACE when
+ * max_entries < n + 1).  Chunk c covers poses first_pose[c] ..
+ * first_pose[c+1]-1, i.e. images[img_offsets[first_pose[c]] ..
+ * img_offsets[first_pose[c+1]]). */
+int diffus_batch_plan_chunks(const void *plan_host, int32_t *first_pose, int32_t max_entries);
 
 /* Forward (and, if grad_images is non-NULL, backward) render of all poses of
  * a plan in persistent launches over a ray queue.  poses (device float

@@ -40,9 +40,12 @@ class ParamsDesc(C.Structure):
                 ("atten", C.c_int32)]
 
 
+MAX_BWD_CHUNKS = 16
+
+
 class ScheduleDesc(C.Structure):
     _fields_ = [("rays_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32), ("brick", C.c_int32),
-                ("fwd_form", C.c_int32)]
+                ("fwd_form", C.c_int32), ("bwd_chunks", C.c_int32)]
 
 
 class ScanGridDesc(C.Structure):
@@ -51,7 +54,8 @@ class ScanGridDesc(C.Structure):
 
 
 class TraceDesc(C.Structure):
-    _fields_ = [("event", C.c_void_p * 10), ("wait_before_bwd", C.c_void_p)]
+    _fields_ = [("event", C.c_void_p * 10), ("wait_before_bwd", C.c_void_p),
+                ("wait_chunk", C.c_void_p * MAX_BWD_CHUNKS)]
 
 
 class DiffusError(RuntimeError):
@@ -87,6 +91,7 @@ def load(build_if_missing: bool = True):
                                           vp, C.c_size_t, p(C.c_int64), p(C.c_size_t), p(C.c_size_t)]
         lib.diffus_render_batch.argtypes = [vp, p(VolumeDesc), vp, vp, vp, p(ParamsDesc), vp, vp, vp, vp, vp, vp,
                                             vp, C.c_size_t, p(TraceDesc), vp]
+        lib.diffus_batch_plan_chunks.argtypes = [vp, p(C.c_int32), C.c_int32]
         lib.diffus_strerror.argtypes = [C.c_int]
         lib.diffus_strerror.restype = C.c_char_p
         lib.diffus_version.restype = C.c_int
@@ -238,11 +243,22 @@ def batch_plan(vol, spacing, origin, fans, params, schedule=None):
     wsf, wsb = C.c_size_t(), C.c_size_t()
     vd = volume_desc(vol, spacing, origin)
     pd = params_desc(params)
-    sd = schedule if schedule is not None else ScheduleDesc(0, 0, 0, 0)
+    sd = schedule if schedule is not None else ScheduleDesc(0, 0, 0, 0, 0)
     rc = lib.diffus_batch_plan(C.byref(vd), farr, P, C.byref(pd), C.byref(sd), C.c_void_p(plan.data_ptr()),
                                int(nbytes), offs.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(wsf), C.byref(wsb))
     _check(rc, "diffus_batch_plan")
     return plan, offs, int(wsf.value), int(wsb.value)
+
+
+def batch_plan_chunks(plan_host):
+    """diffus_batch_plan_chunks (host): the first pose of every backward
+    chunk of a plan, then P (int32 numpy [n + 1])."""
+    lib = load()
+    out = np.zeros(MAX_BWD_CHUNKS + 1, dtype=np.int32)
+    n = lib.diffus_batch_plan_chunks(C.c_void_p(plan_host.data_ptr()), out.ctypes.data_as(C.POINTER(C.c_int32)),
+                                     MAX_BWD_CHUNKS + 1)
+    _check(min(n, 0), "diffus_batch_plan_chunks")
+    return out[:n + 1].copy()
 
 
 def render_batch(vol, spacing, origin, poses, plan_host, plan_dev, params, images, workspace, ray_valid=None,

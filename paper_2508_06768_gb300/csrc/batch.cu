@@ -11,6 +11,8 @@
 #include <numeric>
 #include <vector>
 
+#include <atomic>
+
 #include "host.hpp"
 #include "march_bwd.cuh"
 #include "march_bwd_tile.cuh"
@@ -47,6 +49,12 @@ struct PlanHeader {
         off_tiles, off_ftiles, off_spk;
     int64_t bytes;
     uint64_t params_fp;   // fingerprint of the parameters the plan was made for
+    // backward chunks: chunk c covers poses chunk_pose[c] .. chunk_pose[c+1]-1,
+    // queue entries chunk_q[c] .. chunk_q[c+1]-1 of the ray order and blur
+    // strips chunk_t[c] .. chunk_t[c+1]-1 (both lists are chunk-major)
+    int32_t n_chunks, pad_chunks;
+    int32_t chunk_pose[DIFFUS_MAX_BWD_CHUNKS + 1];
+    int64_t chunk_q[DIFFUS_MAX_BWD_CHUNKS + 1], chunk_t[DIFFUS_MAX_BWD_CHUNKS + 1];
 };
 
 template <typename T>
@@ -122,6 +130,12 @@ int64_t count_spk(const diffus_fan *fans, int P)
     return t;
 }
 
+// Work-queue counters of one call: 0 forward march, 1 adjoint, 2 blur,
+// 3 blur transpose, 4-5 refinement list and tickets, 6-7 spare, then two per
+// backward chunk (blur transpose, adjoint).
+constexpr int kCtrChunk = 8;
+constexpr int kCounters = kCtrChunk + 2 * DIFFUS_MAX_BWD_CHUNKS;
+
 struct BatchLayout {
     RayGeo *geo;
     PoseFrame *frames;
@@ -146,7 +160,7 @@ BatchLayout batch_layout(void *ws, const PlanHeader &H, const diffus_volume_desc
     BatchLayout L;
     L.geo = c.take<RayGeo>((size_t)H.total_rays);
     L.frames = c.take<PoseFrame>((size_t)H.P);
-    L.counter = c.take<unsigned>(8);
+    L.counter = c.take<unsigned>(kCounters);
     L.y = blur ? c.take<float>((size_t)H.total_img) : nullptr;
     // the one-warp-per-ray forward reads speckle factors drawn ahead of it
     const bool spk_ahead = speckle && H.fwd_form == 0;
@@ -346,16 +360,19 @@ __global__ void __launch_bounds__(WARPS * 32, (POSE ? kBwdThreadsPerSM : kBwdVal
                                                           double *__restrict__ part, float4 *__restrict__ ckpt,
                                                           unsigned *__restrict__ counter,
                                                           const float *__restrict__ mbuf,
-                                                          const float2 *__restrict__ kbuf)
+                                                          const float2 *__restrict__ kbuf, int64_t q0, int64_t qn)
 {
-    __shared__ BwdSmem<POSE> sm[WARPS];
+    // WARPS slots of BwdSmem, in dynamic shared memory (above the 48 KB of
+    // static arrays with 8 warps)
+    extern __shared__ __align__(16) unsigned char bwd_smem[];
+    BwdSmem<POSE> *sm = reinterpret_cast<BwdSmem<POSE> *>(bwd_smem);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
         unsigned q = 0;
         if (lane == 0) q = atomicAdd(counter, 1u);
         q = __shfl_sync(0xffffffffu, q, 0);
-        if ((int64_t)q >= B.total_rays) break;
-        const int r = B.order[q];
+        if ((int64_t)q >= qn) break;   // entries q0 .. q0+qn-1 of the ray order
+        const int r = B.order[q0 + q];
         RayGeo rg = geo[r];
         MarchArgs Ap = A;
         if (!A.atten) {   // the depth-gain reading keeps a2 = 1 (lossless systems)
@@ -457,17 +474,41 @@ void launch_fwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const 
                                                                   status, kp.ckpt, sel);
 }
 
-template <typename T, int WARPS>
-void launch_bwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, const float *gy,
-                  float *gz, double *part, float4 *ckpt, unsigned *counter, const float *mbuf, const float2 *kbuf,
-                  int grid, bool pose, cudaStream_t s)
+// Opt the batched adjoint in to its dynamic shared memory, once per kernel
+// and device (the attribute is not a stream operation, so this is safe
+// inside a capture).  Returns nonzero on failure.
+template <typename T, int WARPS, bool POSE>
+int bwd_smem_optin(size_t bytes)
 {
-    if (pose)
-        k_batch_bwd<T, WARPS, true><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, gy, gz, part, ckpt,
-                                                                counter, mbuf, kbuf);
-    else
-        k_batch_bwd<T, WARPS, false><<<grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, gy, gz, part, ckpt,
-                                                                 counter, mbuf, kbuf);
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return 0;
+    if (cudaFuncSetAttribute(k_batch_bwd<T, WARPS, POSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
+        return 1;
+    done.fetch_or(bit, std::memory_order_acq_rel);
+    return 0;
+}
+
+template <typename T, int WARPS>
+int launch_bwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, const float *gy,
+                  float *gz, double *part, float4 *ckpt, unsigned *counter, const float *mbuf, const float2 *kbuf,
+                  int grid, bool pose, int64_t q0, int64_t qn, cudaStream_t s)
+{
+    if (pose) {
+        const size_t sb = WARPS * sizeof(BwdSmem<true>);
+        if (bwd_smem_optin<T, WARPS, true>(sb)) return DIFFUS_E_LAUNCH;
+        k_batch_bwd<T, WARPS, true><<<grid, WARPS * 32, sb, s>>>((const T *)vol, A, B, geo, gy, gz, part, ckpt,
+                                                                 counter, mbuf, kbuf, q0, qn);
+    } else {
+        const size_t sb = WARPS * sizeof(BwdSmem<false>);
+        if (bwd_smem_optin<T, WARPS, false>(sb)) return DIFFUS_E_LAUNCH;
+        k_batch_bwd<T, WARPS, false><<<grid, WARPS * 32, sb, s>>>((const T *)vol, A, B, geo, gy, gz, part, ckpt,
+                                                                  counter, mbuf, kbuf, q0, qn);
+    }
+    return DIFFUS_OK;
 }
 
 template <typename T>
@@ -487,15 +528,17 @@ int launch_fwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev 
 template <typename T>
 int launch_bwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, const float *gy,
                  float *gz, double *part, float4 *ckpt, unsigned *counter, const float *mbuf, const float2 *kbuf,
-                 int grid, bool pose, cudaStream_t s)
+                 int grid, bool pose, int64_t q0, int64_t qn, cudaStream_t s)
 {
     switch (warps) {
-    case 2: launch_bwd_t<T, 2>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, kbuf, grid, pose, s); break;
-    case 4: launch_bwd_t<T, 4>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, kbuf, grid, pose, s); break;
-    case 8: launch_bwd_t<T, 8>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, kbuf, grid, pose, s); break;
+    case 2: return launch_bwd_t<T, 2>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, kbuf, grid, pose, q0, qn,
+                                       s);
+    case 4: return launch_bwd_t<T, 4>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, kbuf, grid, pose, q0, qn,
+                                       s);
+    case 8: return launch_bwd_t<T, 8>(vol, A, B, geo, gy, gz, part, ckpt, counter, mbuf, kbuf, grid, pose, q0, qn,
+                                       s);
     default: return DIFFUS_E_PLAN;
     }
-    return DIFFUS_OK;
 }
 
 }  // namespace
@@ -560,13 +603,16 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     PlanSizes z = plan_sizes(P, total_rays, n_tiles, n_ftiles, n_spk);
     if (plan_bytes < (size_t)z.bytes) return DIFFUS_E_WORKSPACE;
 
-    diffus_schedule sc = sched ? *sched : diffus_schedule{0, 0, 0, 0};
+    diffus_schedule sc = sched ? *sched : diffus_schedule{0, 0, 0, 0, 0};
     if (sc.fwd_form != 0 && sc.fwd_form != 1) return DIFFUS_E_PARAM;
     if (sc.rays_per_cta == 0) sc.rays_per_cta = 4;
-    if (sc.ctas_per_sm == 0) sc.ctas_per_sm = 4;
+    // as many CTAs as the marches' register budget keeps resident
+    if (sc.ctas_per_sm == 0 && (sc.rays_per_cta == 2 || sc.rays_per_cta == 4 || sc.rays_per_cta == 8))
+        sc.ctas_per_sm = kFwdThreadsPerSM / (kWarp * sc.rays_per_cta);
     if (sc.brick == 0) sc.brick = 8;    // gather CTAs per SM
     if (sc.rays_per_cta != 2 && sc.rays_per_cta != 4 && sc.rays_per_cta != 8) return DIFFUS_E_PARAM;
     if (sc.ctas_per_sm < 1 || sc.ctas_per_sm > 32 || sc.brick < 1 || sc.brick > 64) return DIFFUS_E_PARAM;
+    if (sc.bwd_chunks < 0 || sc.bwd_chunks > DIFFUS_MAX_BWD_CHUNKS) return DIFFUS_E_PARAM;
 
     memset(plan_host, 0, (size_t)z.bytes);
     PlanHeader &H = *(PlanHeader *)plan_host;
@@ -597,6 +643,23 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     H.off_ck_off = z.off[8]; H.off_tiles = z.off[9]; H.off_ftiles = z.off[10]; H.off_spk = z.off[11];
     H.bytes = z.bytes;
     H.params_fp = params_fingerprint(prm);
+    {
+        // backward chunks: contiguous pose ranges cut where the running work
+        // (ray-samples) first reaches c/n of the total, each range non-empty
+        const int n = std::max(1, std::min<int>(sc.bwd_chunks, P));
+        std::vector<double> cum((size_t)P + 1, 0.0);
+        for (int p = 0; p < P; p++) cum[p + 1] = cum[p] + (double)fans[p].n_rays * (double)fans[p].n_samples;
+        H.n_chunks = n;
+        H.chunk_pose[0] = 0;
+        for (int c = 1; c < n; c++) {
+            const double target = cum[P] * c / n;
+            int p = (int)(std::lower_bound(cum.begin(), cum.end(), target) - cum.begin());
+            p = std::max(p, H.chunk_pose[c - 1] + 1);
+            p = std::min(p, P - (n - c));
+            H.chunk_pose[c] = p;
+        }
+        H.chunk_pose[n] = P;
+    }
 
     PlanPose *pp = at_mut<PlanPose>(plan_host, H.off_pose);
     double *depth = at_mut<double>(plan_host, H.off_depth);
@@ -644,12 +707,20 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     }
     ray0[P] = (int32_t)r;
     img_offsets[P] = img;
-    // longest rays first; ties in ray order (stable)
+    // chunk of every pose (backward ranges)
+    std::vector<int32_t> chunk_of((size_t)P);
+    for (int c = 0; c < H.n_chunks; c++)
+        for (int p = H.chunk_pose[c]; p < H.chunk_pose[c + 1]; p++) chunk_of[p] = c;
+    // longest rays first within each chunk; ties in ray order (stable)
     std::vector<int32_t> ord((size_t)total_rays);
     std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(),
-                     [&](int32_t x, int32_t y) { return pp[ray_pose[x]].S > pp[ray_pose[y]].S; });
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) {
+        const int cx = chunk_of[ray_pose[x]], cy = chunk_of[ray_pose[y]];
+        if (cx != cy) return cx < cy;
+        return pp[ray_pose[x]].S > pp[ray_pose[y]].S;
+    });
     std::copy(ord.begin(), ord.end(), order);
+    for (int c = 0; c <= H.n_chunks; c++) H.chunk_q[c] = c < H.n_chunks ? ray0[H.chunk_pose[c]] : total_rays;
     // forward tiles longest first (ties in plan order)
     std::stable_sort(ftiles, ftiles + n_ftiles, [](const TileDesc &x, const TileDesc &y) { return x.S > y.S; });
     {
@@ -658,13 +729,36 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
         for (int64_t tix = 0; tix < n_ftiles; tix++)
             for (int k0 = 0; k0 < ftiles[tix].S; k0 += kSpkRows) items[q++] = SpkItem{(int32_t)tix, k0};
     }
-    // blur strips of the widest poses first (a strip's work grows with n_rays)
-    std::stable_sort(tiles, tiles + n_tiles, [](const BlurTile &x, const BlurTile &y) { return x.n_rays > y.n_rays; });
+    // blur strips of the widest poses first within each chunk (a strip's
+    // work grows with n_rays)
+    std::stable_sort(tiles, tiles + n_tiles, [&](const BlurTile &x, const BlurTile &y) {
+        const int cx = chunk_of[x.pose], cy = chunk_of[y.pose];
+        if (cx != cy) return cx < cy;
+        return x.n_rays > y.n_rays;
+    });
+    {
+        int64_t tix = 0;
+        for (int c = 0; c < H.n_chunks; c++) {
+            H.chunk_t[c] = tix;
+            while (tix < n_tiles && chunk_of[tiles[tix].pose] == c) tix++;
+        }
+        H.chunk_t[H.n_chunks] = n_tiles;
+    }
 
     BatchLayout L = batch_layout(nullptr, H, vd, prm->blur != 0, prm->speckle != 0, prm->atten != 0, prm->refine != 0);
     if (ws_fwd) *ws_fwd = L.fwd_bytes;
     if (ws_bwd) *ws_bwd = L.bytes;
     return DIFFUS_OK;
+}
+
+extern "C" int diffus_batch_plan_chunks(const void *plan_host, int32_t *first_pose, int32_t max_entries)
+{
+    if (!plan_host || !first_pose) return DIFFUS_E_NULL;
+    const PlanHeader &H = *(const PlanHeader *)plan_host;
+    if (H.magic != kPlanMagic || H.n_chunks < 1 || H.n_chunks > DIFFUS_MAX_BWD_CHUNKS) return DIFFUS_E_PLAN;
+    if (max_entries < H.n_chunks + 1) return DIFFUS_E_WORKSPACE;
+    for (int c = 0; c <= H.n_chunks; c++) first_pose[c] = H.chunk_pose[c];
+    return H.n_chunks;
 }
 
 extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd, const float *poses,
@@ -708,7 +802,7 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     B.total_rays = H.total_rays;
 
     if (status && cudaMemsetAsync(status, 0, 4 * sizeof(uint32_t), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
-    if (cudaMemsetAsync(L.counter, 0, 8 * sizeof(unsigned), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
+    if (cudaMemsetAsync(L.counter, 0, kCounters * sizeof(unsigned), s) != cudaSuccess) return DIFFUS_E_LAUNCH;
     mark(DIFFUS_TR_START);
     k_pose_frames<<<(H.P + 127) / 128, 128, 0, s>>>(poses, H.P, L.frames);
     k_batch_setup<<<(unsigned)((H.total_rays + 127) / 128), 128, 0, s>>>(L.frames, B, make_place(vd), L.geo);
@@ -763,30 +857,67 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
     if (((uintptr_t)grad_images) % 4 || (grad_vol && ((uintptr_t)grad_vol) % 4) ||
         (grad_poses && ((uintptr_t)grad_poses) % 4))
         return DIFFUS_E_ALIGN;
-    const float *gy = grad_images;
-    if (prm->blur) {
-        launch_batch_blur<true>(grad_images, L.gy, dpose, dtiles, H.n_tiles, bl, tgrid, L.counter + 3, s);
-        gy = L.gy;
-    }
-    if (prm->atten && !prm->blur) {   // the depth gain is its own adjoint (with blur it rides on the blur)
-        k_batch_row_gain<<<rgrid, 256, 0, s>>>(gy, L.gy, B);
-        gy = L.gy;
-    }
-    mark(DIFFUS_TR_MARCH_BWD);
-    // with a volume gradient the gather also forms the pose terms, so the
-    // adjoint march reads the kept samples (march_pose above)
-    if (H.fwd_form == 1 && !march_pose) {
-        // six 2-warp CTAs (two input stages each) fill an SM's shared memory
-        const int bgrid = sm_count() * 6;
-        k_batch_bwd_tiles<<<bgrid, kTileWarpsBwd * 32, 0, s>>>(A, B, at<TileDesc>(plan_dev, H.off_ftiles), H.n_ftiles, gy,
-                                                            L.mbuf, L.kbuf, L.bcar, L.gz, L.counter + 1);
+    auto wait_chunk = [&](int c) {
+        if (trace && c < DIFFUS_MAX_BWD_CHUNKS && trace->wait_chunk[c] &&
+            cudaStreamWaitEvent(s, (cudaEvent_t)trace->wait_chunk[c], 0) != cudaSuccess)
+            return DIFFUS_E_LAUNCH;
+        return DIFFUS_OK;
+    };
+    auto adjoint = [&](const float *gyc, int64_t q0, int64_t qn, unsigned *ctr) {
+        if (vd->dtype == DIFFUS_F32)
+            return launch_bwd_w<float>(H.warps, vol, A, B, L.geo, gyc, L.gz, L.part, L.ckpt, ctr, L.mbuf, L.kbuf, grid,
+                                       march_pose, q0, qn, s);
+        return launch_bwd_w<unsigned short>(H.warps, vol, A, B, L.geo, gyc, L.gz, L.part, L.ckpt, ctr, L.mbuf, L.kbuf,
+                                            grid, march_pose, q0, qn, s);
+    };
+    const bool tile_bwd = H.fwd_form == 1 && !march_pose;
+    // range by range: each chunk's blur transpose and adjoint march after its
+    // event (the depth-gain row pass and the tile backward run whole)
+    const bool chunked = H.n_chunks > 1 && !tile_bwd && !(prm->atten && !prm->blur);
+    if (chunked) {
+        for (int c = 0; c < H.n_chunks; c++) {
+            if ((rc = wait_chunk(c))) return rc;
+            const float *gyc = grad_images;
+            if (prm->blur) {
+                const int64_t t0 = H.chunk_t[c], tn = H.chunk_t[c + 1] - t0;
+                const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((tn + kBlurWarps - 1) / kBlurWarps,
+                                                                              (int64_t)sm_count() * 16));
+                if (tn > 0)
+                    launch_batch_blur<true>(grad_images, L.gy, dpose, dtiles + t0, tn, bl, cgrid,
+                                            L.counter + kCtrChunk + 2 * c, s);
+                gyc = L.gy;
+            }
+            if (c == 0) mark(DIFFUS_TR_MARCH_BWD);
+            const int64_t q0 = H.chunk_q[c], qn = H.chunk_q[c + 1] - q0;
+            if (qn > 0 && (rc = adjoint(gyc, q0, qn, L.counter + kCtrChunk + 2 * c + 1))) return rc;
+        }
         rc = DIFFUS_OK;
-    } else if (vd->dtype == DIFFUS_F32)
-        rc = launch_bwd_w<float>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, L.mbuf, L.kbuf,
-                                 grid, march_pose, s);
-    else
-        rc = launch_bwd_w<unsigned short>(H.warps, vol, A, B, L.geo, gy, L.gz, L.part, L.ckpt, L.counter + 1, L.mbuf,
-                                          L.kbuf, grid, march_pose, s);
+    } else {
+        for (int c = 0; c < H.n_chunks; c++)
+            if ((rc = wait_chunk(c))) return rc;
+        const float *gy = grad_images;
+        if (prm->blur) {
+            launch_batch_blur<true>(grad_images, L.gy, dpose, dtiles, H.n_tiles, bl, tgrid, L.counter + 3, s);
+            gy = L.gy;
+        }
+        if (prm->atten && !prm->blur) {   // the depth gain is its own adjoint (with blur it rides on the blur)
+            k_batch_row_gain<<<rgrid, 256, 0, s>>>(gy, L.gy, B);
+            gy = L.gy;
+        }
+        mark(DIFFUS_TR_MARCH_BWD);
+        // with a volume gradient the gather also forms the pose terms, so the
+        // adjoint march reads the kept samples (march_pose above)
+        if (tile_bwd) {
+            // six 2-warp CTAs (two input stages each) fill an SM's shared memory
+            const int bgrid = sm_count() * 6;
+            k_batch_bwd_tiles<<<bgrid, kTileWarpsBwd * 32, 0, s>>>(A, B, at<TileDesc>(plan_dev, H.off_ftiles),
+                                                                H.n_ftiles, gy, L.mbuf, L.kbuf, L.bcar, L.gz,
+                                                                L.counter + 1);
+            rc = DIFFUS_OK;
+        } else {
+            rc = adjoint(gy, 0, H.total_rays, L.counter + 1);
+        }
+    }
     if (rc) return rc;
     mark(DIFFUS_TR_GATHER);
     if (grad_vol) {

@@ -105,7 +105,10 @@ __device__ __forceinline__ void sample_z(const T *__restrict__ vol, const VolGeo
     float c011 = ldv(p11, 0), c111 = ldv(p11, 1);
     float d1 = c100 - c000, d2 = c010 - c000, d3 = c110 - c000;
     float d4 = c001 - c000, d5 = c101 - c000, d6 = c011 - c000, d7 = c111 - c000;
-    float e00 = fx * d1;
+    // the lone product is rounded on its own (__fmul_rn), so no caller's
+    // inlining can fuse it into the difference below: every kernel that
+    // samples gets the same bits
+    float e00 = __fmul_rn(fx, d1);
     float e10 = fmaf(fx, d3 - d2, d2);
     float e01 = fmaf(fx, d5 - d4, d4);
     float e11 = fmaf(fx, d7 - d6, d6);
@@ -215,7 +218,7 @@ struct Xfer {
 __device__ __forceinline__ Xfer xfer(float r, float a2, int mode)
 {
     Xfer t;
-    float r2 = r * r;
+    float r2 = __fmul_rn(r, r);   // rounded on its own: 1 - r^2 is never fused (same bits in every kernel)
     if (mode == DIFFUS_MODE_LITERAL) {
         float R = fabsf(r);
         t.m00 = a2 * fmaf(-2.0f, r2, 1.0f);
@@ -246,7 +249,7 @@ struct Xfer64 {
 __device__ __forceinline__ Xfer64 xfer64(double r, double a2, int mode)
 {
     Xfer64 t;
-    const double r2 = r * r;
+    const double r2 = __dmul_rn(r, r);
     if (mode == DIFFUS_MODE_LITERAL) {
         const double R = fabs(r);
         t.m00 = a2 * fma(-2.0, r2, 1.0);
@@ -329,11 +332,15 @@ __device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t *rk)
     return c;
 }
 
+// Sum of the four bytes of a word (a 4-way dot product with ones: one
+// integer instruction).
+__device__ __forceinline__ int byte_sum(uint32_t w) { return (int)__dp4a(w, 0x01010101u, 0u); }
+
 // Irwin-Hall(4) normal from the four bytes of a word:
 // (sum of bytes - 510) * sqrt(3)/256 has mean 0 and variance ~1.
 __device__ __forceinline__ float ih_normal(uint32_t w)
 {
-    int s = (int)__vsadu4(w, 0u);
+    int s = byte_sum(w);
     return (float)(s - 510) * 0.0067658234670659f;
 }
 

@@ -17,6 +17,8 @@
 // warp scan (5 shuffle levels) and carried from segment to segment.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace dfs {
@@ -241,12 +243,12 @@ __device__ __forceinline__ void chunk_speckle(const Speckle &sp, int i0, int S, 
     // byte sums of rows i0-4 .. i0+11; the radial normal of row i0+t is the
     // window sum of entries t+4-L .. t+4+L, centred and scaled (integer sums
     // are exact, so the window can move by one add and one subtract)
-    const int su[16] = {(int)__vsadu4(gL.x, 0u), (int)__vsadu4(gL.y, 0u), (int)__vsadu4(gL.z, 0u),
-                        (int)__vsadu4(gL.w, 0u), (int)__vsadu4(gA.x, 0u), (int)__vsadu4(gA.y, 0u),
-                        (int)__vsadu4(gA.z, 0u), (int)__vsadu4(gA.w, 0u), (int)__vsadu4(gB.x, 0u),
-                        (int)__vsadu4(gB.y, 0u), (int)__vsadu4(gB.z, 0u), (int)__vsadu4(gB.w, 0u),
-                        (int)__vsadu4(gR.x, 0u), (int)__vsadu4(gR.y, 0u), (int)__vsadu4(gR.z, 0u),
-                        (int)__vsadu4(gR.w, 0u)};
+    const int su[16] = {byte_sum(gL.x), byte_sum(gL.y), byte_sum(gL.z),
+                        byte_sum(gL.w), byte_sum(gA.x), byte_sum(gA.y),
+                        byte_sum(gA.z), byte_sum(gA.w), byte_sum(gB.x),
+                        byte_sum(gB.y), byte_sum(gB.z), byte_sum(gB.w),
+                        byte_sum(gR.x), byte_sum(gR.y), byte_sum(gR.z),
+                        byte_sum(gR.w)};
     const int L = sp.Lr;
     const bool full = L == 4;   // the default window moves by one add and one subtract
     int Wf = su[0] + su[1] + su[2] + su[3] + su[4] + su[5] + su[6] + su[7] + su[8];
@@ -375,24 +377,33 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
         }
         float y[kChunk];
         if (!REFINE) {
+            // TRACK: the FP32 pass of a refined render also finds the last
+            // row whose conditioning needs the refined states
+            auto echoes = [&](auto track) {
+                constexpr bool TRACK = decltype(track)::value;
 #pragma unroll
-            for (int t = 0; t < kChunk; t++) {
-                const int i = i0 + t;
-                y[t] = 0.0f;
-                if (i < S) {
-                    Xfer x = xfer(rr[t], A.a2, A.mode);
-                    float q = fmaf(b0, x.m01, b1);          // det(A_{i+1})
-                    float e = x.m01 * D * frcp(b1 * q);
-                    if (!(q >= kPoleEps)) first_bad = min(first_bad, i + 1);
-                    if (fminf(b1, q) < need_md) last_need = i;
-                    float nb0 = fmaf(b0, x.m00, b1 * x.m10);
-                    b1 = q;
-                    b0 = nb0;
-                    D *= x.delta;
-                    y[t] = m[t] * e;
-                    nonfinite += !isfinite(y[t]);
+                for (int t = 0; t < kChunk; t++) {
+                    const int i = i0 + t;
+                    y[t] = 0.0f;
+                    if (i < S) {
+                        Xfer x = xfer(rr[t], A.a2, A.mode);
+                        float q = fmaf(b0, x.m01, b1);          // det(A_{i+1})
+                        float e = x.m01 * D * frcp(b1 * q);
+                        if (!(q >= kPoleEps)) first_bad = min(first_bad, i + 1);
+                        if (TRACK && fminf(b1, q) < need_md) last_need = i;
+                        float nb0 = fmaf(b0, x.m00, b1 * x.m10);
+                        b1 = q;
+                        b0 = nb0;
+                        D *= x.delta;
+                        y[t] = m[t] * e;
+                        nonfinite += !isfinite(y[t]);
+                    }
                 }
-            }
+            };
+            if (out.rinfo)
+                echoes(std::true_type{});
+            else
+                echoes(std::false_type{});
         } else {
             // FP32 states b_i, D_i of the chunk as the unrefined path computes them
             float sb0[kChunk + 1], sb1[kChunk + 1], sD[kChunk + 1];

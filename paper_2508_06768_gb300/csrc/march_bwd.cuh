@@ -25,6 +25,7 @@ constexpr int kBwdPad = 289;   // smem_idx(256) + 1
 template <bool POSE>
 struct BwdSmem {
     float zr[kBwdPad], dz[kBwdPad];   // samples base .. base+256 (zref + dz form; STORED: zref + dz, r before)
+    float4 eg[kSeg];                  // echo partials of interface lane*8+t at [t*32 + lane] (both reverse passes)
     float gx[POSE ? kBwdPad : 1], gy[POSE ? kBwdPad : 1], gz[POSE ? kBwdPad : 1];   // dZ/dp (POSE)
     double acc[POSE ? 6 : 1];         // the ray's pose-gradient sums (lane 0)
 };
@@ -220,15 +221,19 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
 #pragma unroll
         for (int t = 0; t < kChunk; t++) ge[t] = (i0 + t < S) ? m[t] * ld_once(gy_row + i0 + t) : 0.0f;
 
-        // C': local reverse pass with zero adjoint at the chunk end
+        // C': local reverse pass with zero adjoint at the chunk end; the
+        // echo partials are kept for the true pass
         float c0 = 0.0f, c1 = 0.0f, dloc = 0.0f;
 #pragma unroll
         for (int t = kChunk - 1; t >= 0; t--) {
             if (i0 + t < S) {
                 Xfer x = xfer(rr[t], A.a2, A.mode);
                 EchoGrad g = echo_grad(b0s[t], b1s[t], Dsv[t], x.m01, ge[t]);
-                float n0 = g.gb0 + fmaf(c0, x.m00, c1 * x.m01);
-                float n1 = g.gb1 + fmaf(c0, x.m10, c1);
+                sm.eg[t * kWarp + lane] = make_float4(g.gb0, g.gb1, g.gD, g.gx);
+                // explicit adds: the partials are not fused here either, as
+                // in the true pass, which reads them back
+                float n0 = __fadd_rn(g.gb0, fmaf(c0, x.m00, c1 * x.m01));
+                float n1 = __fadd_rn(g.gb1, fmaf(c0, x.m10, c1));
                 dloc = fmaf(dloc, x.delta, g.gD);
                 c0 = n0;
                 c1 = n1;
@@ -303,7 +308,8 @@ __device__ void march_bwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                 Xfer x = xfer(r, a2, A.mode);
                 float gm00 = b0s[t] * le0, gm10 = b1s[t] * le0, gm01 = b0s[t] * le1;
                 float gdel = lmu * Dsv[t];
-                EchoGrad g = echo_grad(b0s[t], b1s[t], Dsv[t], x.m01, ge[t]);
+                const float4 gv = sm.eg[t * kWarp + lane];   // written by this lane in C'
+                const EchoGrad g{gv.x, gv.y, gv.z, gv.w};
                 float gr;
                 if (A.mode == DIFFUS_MODE_LITERAL) {
                     float R = fabsf(r);

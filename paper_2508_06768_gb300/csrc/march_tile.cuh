@@ -45,10 +45,10 @@ struct TileSmem {
 // Byte sums of the four words of a Philox group (Irwin-Hall before centring).
 __device__ __forceinline__ void group_sums(uint4 w, int s[4])
 {
-    s[0] = (int)__vsadu4(w.x, 0u);
-    s[1] = (int)__vsadu4(w.y, 0u);
-    s[2] = (int)__vsadu4(w.z, 0u);
-    s[3] = (int)__vsadu4(w.w, 0u);
+    s[0] = byte_sum(w.x);
+    s[1] = byte_sum(w.y);
+    s[2] = byte_sum(w.z);
+    s[3] = byte_sum(w.w);
 }
 
 // Forward of one tile.  Outputs as in RayOut, addressed per lane from the
@@ -227,7 +227,8 @@ struct SpkItem {
 
 struct SpkSmem {
     float m[kWarp * kSpkLd];
-    float zr[kSpkRows], zg[kSpkRows];
+    float2 zrg[kSpkRows];      // per row: Ar z^pr, Ag z^pg
+    uint32_t cell[kSpkRows];   // per row: grain cell (band << 24 | index)
 };
 
 // Speckle factors (Section 2.4) of rows k0 .. k0+63 of the tile's rays,
@@ -246,16 +247,18 @@ __device__ void speckle_item(const Speckle &sp, const TileDesc &tl, int k0, floa
     const uint32_t ray = (uint32_t)(tl.j0 + lane);
     const int n = min(kSpkRows, S - k0);
     const float invS = 1.0f / (float)S;
+    const int kb1 = (S + 3) / 4, kb2 = (2 * S + 3) / 4, kb3 = (3 * S + 3) / 4;
+    // what depends on the row only: depth powers and grain cell, once per item
     for (int e = lane; e < kSpkRows; e += kWarp) {
-        const float lz = __log2f((float)(k0 + e + 1) * invS);
-        sm.zr[e] = sp.Ar * exp2f(sp.pr * lz);
-        sm.zg[e] = sp.Ag * exp2f(sp.pg * lz);
+        const int i = k0 + e;
+        const float lz = __log2f((float)(i + 1) * invS);
+        sm.zrg[e] = make_float2(sp.Ar * exp2f(sp.pr * lz), sp.Ag * exp2f(sp.pg * lz));
+        sm.cell[e] = grain_cell(i, kb1, kb2, kb3, sp.gshift);
     }
     int sm1[4], s0[4];
     group_sums(radial_group(sp, (k0 >> 2) - 1, (int)ray, pose), sm1);
     group_sums(radial_group(sp, k0 >> 2, (int)ray, pose), s0);
     const int L = sp.Lr, off_nr = (2 * L + 1) * 510;
-    const int kb1 = (S + 3) / 4, kb2 = (2 * S + 3) / 4, kb3 = (3 * S + 3) / 4;
     uint32_t cur_grp = 0xffffffffu;
     uint4 gw = make_uint4(0, 0, 0, 0);
     __syncwarp();
@@ -264,27 +267,39 @@ __device__ void speckle_item(const Speckle &sp, const TileDesc &tl, int k0, floa
         if (4 * q >= k0 + n) break;
         int sp1[4];
         group_sums(radial_group(sp, q + 1, (int)ray, pose), sp1);
-        const int w9[12] = {sm1[0], sm1[1], sm1[2], sm1[3], s0[0], s0[1], s0[2], s0[3],
-                            sp1[0], sp1[1], sp1[2], sp1[3]};
+        int Wr[4];   // radial window sums of rows 4q .. 4q+3 (exact integers)
+        if (L == 4) {
+            // row 4q's window spans groups q-1 .. q+1 but the last three
+            // rows; each later row drops one byte sum and takes the next
+            Wr[0] = ((sm1[0] + sm1[1]) + (sm1[2] + sm1[3])) + ((s0[0] + s0[1]) + (s0[2] + s0[3])) + sp1[0];
+#pragma unroll
+            for (int t = 1; t < 4; t++) Wr[t] = Wr[t - 1] + (sp1[t] - sm1[t - 1]);
+        } else {
+            const int w9[12] = {sm1[0], sm1[1], sm1[2], sm1[3], s0[0], s0[1], s0[2], s0[3],
+                                sp1[0], sp1[1], sp1[2], sp1[3]};
+#pragma unroll
+            for (int t = 0; t < 4; t++) {
+                int W = w9[t + 4];
+#pragma unroll
+                for (int d = 1; d <= 4; d++)
+                    if (d <= L) W += w9[t + 4 - d] + w9[t + 4 + d];
+                Wr[t] = W;
+            }
+        }
 #pragma unroll
         for (int t = 0; t < 4; t++) {
             const int i = 4 * q + t;
             if (i >= k0 + n) break;
-            int W = w9[t + 4];
-#pragma unroll
-            for (int d = 1; d <= 4; d++)
-                if (d <= L) W += w9[t + 4 - d] + w9[t + 4 + d];
-            const float nr = (float)(W - off_nr) * sp.nr_scale;
-            const int b = (i >= kb1) + (i >= kb2) + (i >= kb3);
-            const int kbb = b == 0 ? 0 : (b == 1 ? kb1 : (b == 2 ? kb2 : kb3));
-            const uint32_t cell = ((uint32_t)b << 24) | (uint32_t)((i - kbb) >> (sp.gshift + b));
+            const float nr = (float)(Wr[t] - off_nr) * sp.nr_scale;
+            const int e = i - k0;
+            const uint32_t cell = sm.cell[e];
             if ((cell >> 2) != cur_grp) {   // the same row for every lane
                 cur_grp = cell >> 2;
                 gw = philox10_rk(make_uint4(cur_grp, ray, pose, 1u), sp.rk);
             }
             const float ng = ih_normal(pick4(gw, cell & 3u));
-            const int e = i - k0;
-            sm.m[lane * kSpkLd + e] = fmaxf(fmaf(sm.zr[e], nr, fmaf(sm.zg[e], ng, 1.0f)), 0.0f);
+            const float2 zrg = sm.zrg[e];
+            sm.m[lane * kSpkLd + e] = fmaxf(fmaf(zrg.x, nr, fmaf(zrg.y, ng, 1.0f)), 0.0f);
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {

@@ -63,6 +63,9 @@ class BatchRenderer:
         self.schedule = schedule
         dev = volume.device
         plan, offs, wsf, wsb = B.batch_plan(self.volume, spacing, origin, self.fans, params, schedule)
+        # first pose of every backward chunk, then P (one chunk unless the
+        # schedule asks for bwd_chunks > 1)
+        self.chunk_poses = B.batch_plan_chunks(plan)
         self.plan_host = plan.pin_memory() if torch.cuda.is_available() else plan
         self.plan_dev = plan.to(dev)
         self.offsets = offs
@@ -78,6 +81,13 @@ class BatchRenderer:
     @property
     def n_ray_samples(self) -> int:
         return int(self.offsets[-1])
+
+    def chunk_ranges(self):
+        """Image-buffer ranges [(start, end)] of the backward chunks: a caller
+        that uploads dL/dimage range by range records trace.wait_chunk[c]
+        after range c's copy."""
+        c = self.chunk_poses
+        return [(int(self.offsets[c[i]]), int(self.offsets[c[i + 1]])) for i in range(len(c) - 1)]
 
     def image(self, p: int) -> torch.Tensor:
         f = self.fans[p]

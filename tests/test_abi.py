@@ -87,3 +87,43 @@ def test_batch_workspace_covers_the_adjoint_state(lib):
     samples = sum(f.n_rays * (f.n_samples + 1) for f in fans)
     assert int(offs[-1]) == rows
     assert wsb - wsf >= (8 + 4) * samples + (4 + 4) * rows
+
+
+def test_backward_chunks_of_a_plan(lib):
+    # host-only planning: bwd_chunks cuts the poses into contiguous,
+    # non-empty ranges where the running work first reaches c/n of the total
+    import math
+    import numpy as np
+    import torch
+    from paper_2508_06768_gb300 import inputs as I
+    vol = torch.zeros((20, 18, 16), dtype=torch.float32)
+    rng = np.random.default_rng(3)
+    fans = [I.Fan(int(rng.integers(1, 40)), int(rng.integers(10, 400)), math.radians(40), 20.0, 5.0, 0.5)
+            for _ in range(37)]
+    work = np.array([f.n_rays * f.n_samples for f in fans], dtype=np.float64)
+    cum = np.concatenate([[0.0], np.cumsum(work)])
+    prm = I.Params(seed=1)
+    plan, _, _, _ = B.batch_plan(vol, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0), fans, prm)
+    assert list(B.batch_plan_chunks(plan)) == [0, len(fans)]   # default: one chunk
+    for n in (2, 5, 16):
+        plan, _, _, _ = B.batch_plan(vol, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0), fans, prm,
+                                     B.ScheduleDesc(0, 0, 0, 0, n))
+        first = B.batch_plan_chunks(plan)
+        assert len(first) == n + 1 and first[0] == 0 and first[-1] == len(fans)
+        assert np.all(np.diff(first) >= 1)
+        for c in range(1, n):
+            # the first pose whose preceding work reaches c/n of the total
+            want = int(np.searchsorted(cum, cum[-1] * c / n, side="left"))
+            assert first[c] == min(max(want, first[c - 1] + 1), len(fans) - (n - c)), (n, c)
+    # more chunks than poses: one pose per chunk
+    plan, _, _, _ = B.batch_plan(vol, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0), fans[:3], prm, B.ScheduleDesc(0, 0, 0, 0, 8))
+    assert list(B.batch_plan_chunks(plan)) == [0, 1, 2, 3]
+    with pytest.raises(B.DiffusError):
+        B.batch_plan(vol, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0), fans, prm, B.ScheduleDesc(0, 0, 0, 0, 17))
+    L = B.load()
+    buf = (C.c_int32 * 4)()
+    assert L.diffus_batch_plan_chunks(None, buf, 4) == -1
+    junk = (C.c_uint8 * 4096)()
+    assert L.diffus_batch_plan_chunks(C.cast(junk, C.c_void_p), buf, 4) == -8
+    plan, _, _, _ = B.batch_plan(vol, (1.0, 1.0, 1.0), (0.0, 0.0, 0.0), fans, prm, B.ScheduleDesc(0, 0, 0, 0, 5))
+    assert L.diffus_batch_plan_chunks(C.c_void_p(plan.data_ptr()), buf, 4) == -6   # needs 6 entries

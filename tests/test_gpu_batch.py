@@ -1,7 +1,7 @@
 """Batched persistent path: agreement with the single-pose entry points
-(bitwise for the warp-per-ray forward form, to rounding for the default
+(bitwise for the default warp-per-ray forward form, to rounding for the
 lane-per-ray form), parity with the oracle on sampled poses and on ragged
-tiles, CUDA-graph replay and schedule independence."""
+tiles, CUDA-graph replay, schedule independence and the chunked backward."""
 import math
 
 import numpy as np
@@ -307,3 +307,52 @@ def test_pipelined_transfers_match_plain_run():
         assert torch.equal(img_h, ref[0])
         assert torch.equal(r.grad_vol.cpu(), ref[1])
         assert torch.equal(r.grad_poses.cpu(), ref[2])
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_backward_chunks_match_one_chunk(form):
+    # bwd_chunks = 4: dL/dimage uploaded range by range on another stream,
+    # each range's event releasing its blur transpose and adjoint march; the
+    # images and both gradients equal a one-chunk run bitwise (the chunks
+    # change the order of independent rays only), also for a pose-only call
+    import torch
+    from paper_2508_06768_gb300 import binding as B
+    vol, poses, fans, prm = _workload(mode=0, count=9, seed=37)
+    r1 = _renderer(vol, fans, prm, sched=B.ScheduleDesc(4, 6, 8, form, 1))
+    r4 = _renderer(vol, fans, prm, sched=B.ScheduleDesc(4, 6, 8, form, 4))
+    assert len(r4.chunk_ranges()) == 4 and r4.chunk_ranges()[-1][1] == r4.n_ray_samples
+    total = r1.n_ray_samples
+    G_h = torch.from_numpy(I.random_weights((total,), 71)).pin_memory()
+    pd = torch.from_numpy(poses).cuda()
+    r1.run(pd, G_h.cuda())
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    up = torch.cuda.Stream()
+    evs = [torch.cuda.Event() for _ in range(4)]
+    for e in evs:
+        e.record(s)
+    tr = B.TraceDesc()
+    for c, e in enumerate(evs):
+        tr.wait_chunk[c] = e.cuda_event
+    G = torch.empty(total, dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        G.fill_(float("nan"))        # a range used before its copy would poison the gradients
+        up.wait_stream(s)
+        with torch.cuda.stream(up):
+            for c, (a, b) in enumerate(r4.chunk_ranges()):
+                G[a:b].copy_(G_h[a:b], non_blocking=True)
+                evs[c].record(up)
+        r4.run(pd, G, stream=s, trace=tr)
+        s.wait_stream(up)
+        torch.cuda.synchronize()
+        assert torch.equal(r4.images, r1.images)
+        assert torch.equal(r4.ray_valid, r1.ray_valid)
+        assert torch.equal(r4.grad_vol, r1.grad_vol)
+        assert torch.equal(r4.grad_poses, r1.grad_poses)
+    # pose-only calls (the adjoint march forms the pose terms)
+    gp1, gp4 = torch.empty_like(r1.grad_poses), torch.empty_like(r4.grad_poses)
+    for r, gp in ((r1, gp1), (r4, gp4)):
+        B.render_batch(r.volume, r.spacing, r.origin, pd, r.plan_host, r.plan_dev, r.params, r.images, r.workspace,
+                       ray_valid=r.ray_valid, grad_images=G, grad_vol=None, grad_poses=gp, status=r.status)
+    torch.cuda.synchronize()
+    assert torch.equal(gp4, gp1)
