@@ -111,10 +111,13 @@ typedef struct {
  *    max(0.05, 0.0025 sqrt(S)) (where its FP32 error may exceed 1e-5) or
  *    the ray meets a pole.  The refined pass redoes such a ray up to its last such
  *    row (at least to the pole, whose decision it takes again): residuals
- *    of the FP32 depth recurrence are computed in FP64 against coefficients
- *    from FP64 samples at the FP64 ray positions, the error recurrence is
- *    solved in FP32 and the echoes use the corrected states.  Any volume
- *    dtype, single-pose and batched forward; the adjoint stays FP32.
+ *    of the FP32 depth recurrence are computed in double-single arithmetic
+ *    (pairs of floats, about 47 significant bits, in place of FP64, which
+ *    runs at 1/64 of the FP32 rate on this part) against coefficients from
+ *    double-single samples at the FP64 ray line's positions, the error
+ *    recurrence is solved in FP32 and the echoes use the corrected states.
+ *    Any volume dtype, single-pose and batched forward; the adjoint stays
+ *    FP32.
  *  atten (the two readings of "uniform attenuation", Section 2.1): 0 puts
  *    the amplitude factor a = 10^(-alpha f ds / 20) of every sample cell
  *    inside the rows of Eq. 4 (default); 1 solves the depth systems with

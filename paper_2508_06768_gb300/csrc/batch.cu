@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(kTileWarps * 32) k_batch_speckle(Speckle sp, c
 // Refined pass of the batch over the rays the FP32 pass listed (in the order
 // it listed them, which follows its longest-first queue).
 template <typename T, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 1) k_batch_refine(const T *__restrict__ vol, MarchArgs A, BatchDev B,
+__global__ void __launch_bounds__(WARPS * 32, kRefineWarpsPerSM / WARPS) k_batch_refine(const T *__restrict__ vol, MarchArgs A, BatchDev B,
                                                                 const RayGeo *__restrict__ geo,
                                                                 const PoseFrame *__restrict__ frames, VolPlace vp,
                                                                 float *__restrict__ out, int *__restrict__ valid,
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) k_batch_refine(const T *__restr
                                                                 float4 *__restrict__ ckpt, RefineSel sel)
 {
     __shared__ float buf[WARPS][kSegPad];
-    __shared__ double dbuf[WARPS][kSegPad];
+    __shared__ float2 dbuf[WARPS][kSegPad];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned n = *sel.rcount;
     for (;;) {
@@ -470,7 +470,7 @@ void launch_fwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const 
         k_batch_fwd<T, WARPS><<<fl.grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status, counter,
                                                              kp.ckpt, kp.mbuf, kp.kbuf, fl.spk_in, sel);
     if (sel.rinfo)
-        k_batch_refine<T, WARPS><<<2 * sm_count(), WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, frames, vp, out, valid,
+        k_batch_refine<T, WARPS><<<kRefineWarpsPerSM / WARPS * sm_count(), WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, frames, vp, out, valid,
                                                                   status, kp.ckpt, sel);
 }
 

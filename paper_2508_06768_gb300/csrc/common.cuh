@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "diffus.h"
+#include "ff.cuh"
 
 namespace dfs {
 
@@ -87,7 +88,7 @@ __device__ __forceinline__ void axis_split(long long X, int n, int &i0, float &f
 template <typename T, bool GRAD>
 __device__ __forceinline__ void sample_z(const T *__restrict__ vol, const VolGeo &g, long long X,
                                          long long Y, long long Zc, float &zref, float &dz,
-                                         float *grad = nullptr)
+                                         float *grad = nullptr, float *corners = nullptr)
 {
     int ix, iy, iz;
     float fx, fy, fz;
@@ -103,6 +104,10 @@ __device__ __forceinline__ void sample_z(const T *__restrict__ vol, const VolGeo
     float c010 = ldv(p10, 0), c110 = ldv(p10, 1);
     float c001 = ldv(p01, 0), c101 = ldv(p01, 1);
     float c011 = ldv(p11, 0), c111 = ldv(p11, 1);
+    if (corners) {   // the cell's corners for a second evaluation (the refined pass)
+        corners[0] = c000; corners[1] = c100; corners[2] = c010; corners[3] = c110;
+        corners[4] = c001; corners[5] = c101; corners[6] = c011; corners[7] = c111;
+    }
     float d1 = c100 - c000, d2 = c010 - c000, d3 = c110 - c000;
     float d4 = c001 - c000, d5 = c101 - c000, d6 = c011 - c000, d7 = c111 - c000;
     // the lone product is rounded on its own (__fmul_rn), so no caller's
@@ -133,42 +138,45 @@ __device__ __forceinline__ void sample_z(const T *__restrict__ vol, const VolGeo
     }
 }
 
-// Impedance in FP64 for the residual of the refinement pass: the trilinear
-// form of the cell that the fixed-point position (X, Y, Zc) selects, with
-// FP64 lerps of the stored corners and FP64 weights taken from the ray's
-// FP64 position p (voxel coordinates of the same sample without the
-// fixed-point rounding, as the FP64 definition samples it).  An axis whose
-// fixed-point coordinate is clamped (outside [0, n-1]) keeps the clamped
-// weight 0 or 1.  Near a cell face the two positions may select
-// neighbouring cells; the trilinear field is continuous there, so the value
-// moves only by the rounding distance times the jump of its slope.
-__device__ __forceinline__ double axis_w64(long long X, int n, double x, int &i0)
+// Impedance in double-single precision for the residual of the refinement
+// pass: the trilinear form of the cell that the fixed-point position
+// (X, Y, Zc) selects, with double-single lerps of the stored corners and
+// double-single weights taken from the ray's FP64 line p (voxel coordinates
+// of the same sample without the fixed-point rounding, as the FP64
+// definition samples it).  An axis whose fixed-point coordinate is clamped
+// (outside [0, n-1]) keeps the clamped weight 0 or 1.  Near a cell face the
+// two positions may select neighbouring cells; the trilinear field is
+// continuous there, so the value moves only by the rounding distance times
+// the jump of its slope.
+__device__ __forceinline__ FF axis_w_ff(long long X, int n, FF x, int &i0)
 {
     const int hi = (int)(X >> 32);
     const bool below = X < 0, above = hi >= n - 1;
     i0 = below ? 0 : (above ? n - 2 : hi);
-    return below ? 0.0 : (above ? 1.0 : x - (double)i0);
+    if (below) return {0.0f, 0.0f};
+    if (above) return {1.0f, 0.0f};
+    const FF w = two_sum(x.h, -(float)i0);
+    return {w.h, __fadd_rn(w.l, x.l)};
 }
 
-template <typename T>
-__device__ __forceinline__ double sample_z64(const T *__restrict__ vol, const VolGeo &g, long long X, long long Y,
-                                             long long Zc, double px, double py, double pz)
+// c: the cell's corners as sample_z returns them (the same cell: both
+// select it from the same fixed-point coordinates).
+__device__ __forceinline__ FF sample_z_ff(const float *c, const VolGeo &g, long long X, long long Y, long long Zc,
+                                          FF px, FF py, FF pz)
 {
     int ix, iy, iz;
-    const double fx = axis_w64(X, g.nx, px, ix);
-    const double fy = axis_w64(Y, g.ny, py, iy);
-    const double fz = axis_w64(Zc, g.nz, pz, iz);
-    const unsigned sy = (unsigned)g.nx, sz = (unsigned)g.nx * (unsigned)g.ny;
-    const unsigned o = (unsigned)iz * sz + (unsigned)iy * sy + (unsigned)ix;
-    const double c000 = ldv(vol, o), c100 = ldv(vol, o + 1);
-    const double c010 = ldv(vol, o + sy), c110 = ldv(vol, o + sy + 1);
-    const double c001 = ldv(vol, o + sz), c101 = ldv(vol, o + sz + 1);
-    const double c011 = ldv(vol, o + sz + sy), c111 = ldv(vol, o + sz + sy + 1);
-    const double c00 = fma(fx, c100 - c000, c000), c10 = fma(fx, c110 - c010, c010);
-    const double c01 = fma(fx, c101 - c001, c001), c11 = fma(fx, c111 - c011, c011);
-    const double c0 = fma(fy, c10 - c00, c00), c1 = fma(fy, c11 - c01, c01);
-    return fma(fz, c1 - c0, c0);
+    const FF fx = axis_w_ff(X, g.nx, px, ix);
+    const FF fy = axis_w_ff(Y, g.ny, py, iy);
+    const FF fz = axis_w_ff(Zc, g.nz, pz, iz);
+    const FF c00 = ff_lerp(ff_from(c[0]), ff_from(c[1]), fx), c10 = ff_lerp(ff_from(c[2]), ff_from(c[3]), fx);
+    const FF c01 = ff_lerp(ff_from(c[4]), ff_from(c[5]), fx), c11 = ff_lerp(ff_from(c[6]), ff_from(c[7]), fx);
+    const FF c0 = ff_lerp(c00, c10, fy), c1 = ff_lerp(c01, c11, fy);
+    return ff_lerp(c0, c1, fz);
 }
+
+// Signed reflection coefficient (Z2 - Z1)/(Z1 + Z2) of Eq. 1 in
+// double-single precision.
+__device__ __forceinline__ FF refl_ff(FF z1, FF z2) { return ff_div(ff_sub(z2, z1), ff_add(z2, z1)); }
 
 // Round-trip depth gain a^(2(k+1)) = 2^((k+1) l2) of echo row k under the
 // depth-gain reading of attenuation, l2 = log2(a^2) = l2_hi + l2_lo.  The
@@ -233,34 +241,30 @@ __device__ __forceinline__ Xfer xfer(float r, float a2, int mode)
     return t;
 }
 
-// FP64 interface coefficient and transfer entries, recomputed from the
-// same FP32 sample pairs for the residual of the refinement pass.
-__device__ __forceinline__ double refl64(float zr1, float dz1, float zr2, float dz2)
-{
-    const double dZ = ((double)zr2 - (double)zr1) + ((double)dz2 - (double)dz1);
-    const double sZ = ((double)zr1 + (double)dz1) + ((double)zr2 + (double)dz2);
-    return dZ / sZ;
-}
-
-struct Xfer64 {
-    double m00, m01, m10, delta;
+// Transfer entries of one interface in double-single precision (the
+// refined pass's residuals), the same formulas as xfer.
+struct XferFF {
+    FF m00, m01, m10, delta;
 };
 
-__device__ __forceinline__ Xfer64 xfer64(double r, double a2, int mode)
+__device__ __forceinline__ XferFF xfer_ff(FF r, FF a2, int mode)
 {
-    Xfer64 t;
-    const double r2 = __dmul_rn(r, r);
+    XferFF t;
+    const FF r2 = ff_mul(r, r);
+    const FF one_m_r2 = ff_add(ff_from(1.0f), ff_neg(r2));
     if (mode == DIFFUS_MODE_LITERAL) {
-        const double R = fabs(r);
-        t.m00 = a2 * fma(-2.0, r2, 1.0);
-        t.m01 = a2 * R;
-        t.m10 = -R;
+        const bool neg = r.h < 0.0f || (r.h == 0.0f && r.l < 0.0f);
+        const FF R = neg ? ff_neg(r) : r;
+        const FF one_m_2r2 = ff_add(ff_from(1.0f), ff_mul_f(r2, -2.0f));
+        t.m00 = ff_mul(a2, one_m_2r2);
+        t.m01 = ff_mul(a2, R);
+        t.m10 = ff_neg(R);
     } else {
         t.m00 = a2;
-        t.m01 = a2 * r;
+        t.m01 = ff_mul(a2, r);
         t.m10 = r;
     }
-    t.delta = a2 * (1.0 - r2);
+    t.delta = ff_mul(a2, one_m_r2);
     return t;
 }
 

@@ -50,6 +50,29 @@ struct RayLine64 {
     double x0[3], dx[3];
 };
 
+// The same line in double-single precision.
+struct RayLineFF {
+    FF x0[3], dx[3];
+};
+
+__device__ __forceinline__ RayLineFF line_ff(const RayLine64 &l)
+{
+    RayLineFF f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        f.x0[a] = ff_from_double(l.x0[a]);
+        f.dx[a] = ff_from_double(l.dx[a]);
+    }
+    return f;
+}
+
+// x0 + k dx in double-single precision (k < 2^24 is exact as a float).
+__device__ __forceinline__ FF line_pos(FF x0, FF dx, float kf)
+{
+    const FF a = two_prod(kf, dx.h);
+    const FF s = two_sum(x0.h, a.h);
+    return {s.h, __fadd_rn(s.l, __fadd_rn(a.l, __fmaf_rn(kf, dx.l, x0.l)))};
+}
 struct RayOut {
     float *row;       // output row [S] (image or pre-blur buffer)
     int *valid;       // nullable: leading pole-free rows
@@ -78,19 +101,20 @@ __device__ __forceinline__ void sample_pos(const RayGeo &rg, int k, long long &X
 // writes r_i (i = base..base+255, 0 past the ray) into buf[smem_idx(i-base)].
 // (czr, cdz) carries the sample at `base` in and the one at base+256 out.
 // krow (nullable) also receives, per sample k, (zref + dz, r_{k-1}).
-// REFINE (the refined pass) also writes r_i in FP64 into dbuf, from FP64
-// samples (sample_z64) at the FP64 positions of `line`; cz64 carries the
-// FP64 sample at `base` in and the one at base+256 out.
+// REFINE (the refined pass) also writes r_i in double-single precision into
+// dbuf (h, l), from double-single samples (sample_z_ff) at the FP64-line
+// positions of `line`; czf carries that sample at `base` in and the one at
+// base+256 out.
 template <typename T, bool REFINE = false>
 __device__ __forceinline__ void seg_reflections(const T *__restrict__ vol, const VolGeo &g, const RayGeo &rg,
                                                 int base, float &czr, float &cdz, float *__restrict__ buf,
-                                                double *__restrict__ dbuf = nullptr, float2 *__restrict__ krow = nullptr,
-                                                const RayLine64 *line = nullptr, double *cz64 = nullptr)
+                                                float2 *__restrict__ dbuf = nullptr, float2 *__restrict__ krow = nullptr,
+                                                const RayLineFF *line = nullptr, FF *czf = nullptr)
 {
     const int lane = threadIdx.x & 31;
     const int S = rg.S;
     float pzr = czr, pdz = cdz;
-    double pz64 = REFINE ? *cz64 : 0.0;
+    FF pzf = REFINE ? *czf : FF{0.0f, 0.0f};
     long long X, Y, Z;
     sample_pos(rg, base + lane + 1, X, Y, Z);
     const long long sX = rg.DX[0] * kWarp, sY = rg.DX[1] * kWarp, sZ = rg.DX[2] * kWarp;
@@ -98,13 +122,14 @@ __device__ __forceinline__ void seg_reflections(const T *__restrict__ vol, const
     for (int t = 0; t < kChunk; t++) {
         int k = base + t * kWarp + lane + 1;
         float zr = 0.0f, dz = 0.0f;
-        double z64 = 0.0;
+        FF zf{0.0f, 0.0f};
         if (k <= S) {
-            sample_z<T, false>(vol, g, X, Y, Z, zr, dz);
+            float cor[8];
+            sample_z<T, false>(vol, g, X, Y, Z, zr, dz, nullptr, REFINE ? cor : nullptr);
             if (REFINE) {
-                const double kd = (double)k;
-                z64 = sample_z64<T>(vol, g, X, Y, Z, fma(kd, line->dx[0], line->x0[0]),
-                                    fma(kd, line->dx[1], line->x0[1]), fma(kd, line->dx[2], line->x0[2]));
+                const float kf = (float)k;
+                zf = sample_z_ff(cor, g, X, Y, Z, line_pos(line->x0[0], line->dx[0], kf),
+                                 line_pos(line->x0[1], line->dx[1], kf), line_pos(line->x0[2], line->dx[2], kf));
             }
         }
         X += sX;
@@ -117,17 +142,18 @@ __device__ __forceinline__ void seg_reflections(const T *__restrict__ vol, const
         buf[smem_idx(t * kWarp + lane)] = r;
         if (krow && k <= S) __stcs(krow + k, make_float2(zr + dz, r));
         if (REFINE) {
-            double lz64 = __shfl_up_sync(0xffffffffu, z64, 1);
-            if (lane == 0) lz64 = pz64;
-            dbuf[smem_idx(t * kWarp + lane)] = (k - 1 < S) ? (z64 - lz64) / (z64 + lz64) : 0.0;
-            pz64 = __shfl_sync(0xffffffffu, z64, 31);
+            FF lzf{__shfl_up_sync(0xffffffffu, zf.h, 1), __shfl_up_sync(0xffffffffu, zf.l, 1)};
+            if (lane == 0) lzf = pzf;
+            const FF rf = (k - 1 < S) ? refl_ff(lzf, zf) : FF{0.0f, 0.0f};
+            dbuf[smem_idx(t * kWarp + lane)] = make_float2(rf.h, rf.l);
+            pzf = FF{__shfl_sync(0xffffffffu, zf.h, 31), __shfl_sync(0xffffffffu, zf.l, 31)};
         }
         pzr = __shfl_sync(0xffffffffu, zr, 31);
         pdz = __shfl_sync(0xffffffffu, dz, 31);
     }
     czr = pzr;
     cdz = pdz;
-    if (REFINE) *cz64 = pz64;
+    if (REFINE) *czf = pzf;
 }
 
 // Chunk product Q = M_{i0} ... M_{i0+7} (identity past the ray) and its
@@ -284,7 +310,7 @@ __device__ __forceinline__ void chunk_speckle(const Speckle &sp, int i0, int S, 
 }
 
 // Forward march of one ray by one warp.  buf: this warp's shared row of
-// kSegPad floats; dbuf: kSegPad doubles when REFINE.  STREAM writes the
+// kSegPad floats; dbuf: kSegPad float pairs when REFINE.  STREAM writes the
 // output row with evict-first stores (the batched kernel).
 //
 // Without REFINE (the FP32 pass) and with out.rinfo set, the march also
@@ -296,29 +322,35 @@ __device__ __forceinline__ void chunk_speckle(const Speckle &sp, int i0, int S, 
 // pass recorded) redoes the first segments of the ray with one
 // iterative-refinement pass of the depth recurrence b_{i+1} = b_i M_i,
 // D_{i+1} = D_i delta_i: the FP32 states are kept, their residuals
-// rho_{i+1} = b_i M*_i - b_{i+1} are computed in FP64 with M*_i the FP64
-// coefficients of FP64 samples (sample_z64), the error recurrence
+// rho_{i+1} = b_i M*_i - b_{i+1} are computed in double-single precision
+// (about 47 bits, ff.cuh) with M*_i the coefficients of double-single samples
+// at the FP64 line's positions (sample_z_ff), the error recurrence
 // e_{i+1} = e_i M_i + rho_{i+1} (e_0 = 0) of e_i = b*_i - b_i (b* the states
-// of the FP64 coefficients) is solved in FP32 with the same scan (affine
-// maps), and the echoes use the corrected states b_i + e_i and the FP64
+// of the exact coefficients) is solved in FP32 with the same scan (affine
+// maps), and the echoes use the corrected states b_i + e_i and the refined
 // coefficient x*_i.  It covers rinfo.x segments, and goes on while the FP32
 // pass saw a pole there that the refined states do not confirm; rows beyond
 // keep the FP32 pass's values.
 template <typename T, bool REFINE = false, bool STREAM = false>
 __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, const RayGeo &rg,
-                              const RayOut &out, float *__restrict__ buf, double *__restrict__ dbuf = nullptr,
-                              const RayLine64 *line = nullptr, int2 rinfo = make_int2(0, 0))
+                              const RayOut &out, float *__restrict__ buf, float2 *__restrict__ dbuf = nullptr,
+                              const RayLine64 *line64 = nullptr, int2 rinfo = make_int2(0, 0))
 {
     const int lane = threadIdx.x & 31;
     const int S = rg.S;
     const uint32_t pose = A.sp.pose_ctr + (uint32_t)rg.pose;
     const int nseg = (S + kSeg - 1) / kSeg;
 
-    float czr, cdz;
-    sample_z<T, false>(vol, A.g, rg.X0[0], rg.X0[1], rg.X0[2], czr, cdz);
-    double cz64 = 0.0;
-    if (REFINE)
-        cz64 = sample_z64<T>(vol, A.g, rg.X0[0], rg.X0[1], rg.X0[2], line->x0[0], line->x0[1], line->x0[2]);
+    float czr, cdz, cor0[8];
+    sample_z<T, false>(vol, A.g, rg.X0[0], rg.X0[1], rg.X0[2], czr, cdz, nullptr, REFINE ? cor0 : nullptr);
+    RayLineFF line_f;
+    FF czf{0.0f, 0.0f};
+    FF a2f{0.0f, 0.0f};
+    if (REFINE) {
+        line_f = line_ff(*line64);
+        czf = sample_z_ff(cor0, A.g, rg.X0[0], rg.X0[1], rg.X0[2], line_f.x0[0], line_f.x0[1], line_f.x0[2]);
+        a2f = ff_from_double(A.a2d);
+    }
     if (!REFINE && out.krow && lane == 0) out.krow[0] = make_float2(czr + cdz, 0.0f);
     float bs0 = 0.0f, bs1 = 1.0f, Ds = 1.0f;   // bottom row and det at segment start
     int first_bad = 0x7fffffff;
@@ -339,8 +371,8 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
         }
         const int base = seg * kSeg;
         if (out.ckpt && lane == 0) out.ckpt[seg] = make_float4(bs0 + es0, bs1 + es1, Ds + esD, 0.0f);
-        seg_reflections<T, REFINE>(vol, A.g, rg, base, czr, cdz, buf, dbuf, REFINE ? nullptr : out.krow, line,
-                                   &cz64);
+        seg_reflections<T, REFINE>(vol, A.g, rg, base, czr, cdz, buf, dbuf, REFINE ? nullptr : out.krow, &line_f,
+                                   &czf);
         __syncwarp();
         const int i0 = base + lane * kChunk;
         float rr[kChunk];
@@ -439,7 +471,7 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                     sD[kChunk] = nD;
                 }
             }
-            // FP64 residuals and the chunk's local correction map e -> e Q + c
+            // double-single residuals and the chunk's local correction map e -> e Q + c
             float rho0[kChunk], rho1[kChunk], rhoD[kChunk], xs[kChunk];
             float c0 = 0.0f, c1 = 0.0f, cD = 0.0f;
 #pragma unroll
@@ -447,13 +479,13 @@ __device__ void march_fwd_ray(const T *__restrict__ vol, const MarchArgs &A, con
                 rho0[t] = rho1[t] = rhoD[t] = 0.0f;
                 xs[t] = 0.0f;
                 if (i0 + t < S) {
-                    const Xfer64 x = xfer64(dbuf[smem_idx(lane * kChunk + t)], A.a2d, A.mode);
-                    const double p0 = sb0[t], p1 = sb1[t];
+                    const float2 rv = dbuf[smem_idx(lane * kChunk + t)];
+                    const XferFF x = xfer_ff(FF{rv.x, rv.y}, a2f, A.mode);
                     // rho = b_i M*_i - b_{i+1}: what the FP32 step lost
-                    rho0[t] = (float)(fma(p0, x.m00, p1 * x.m10) - (double)sb0[t + 1]);
-                    rho1[t] = (float)(fma(p0, x.m01, p1) - (double)sb1[t + 1]);
-                    rhoD[t] = (float)((double)sD[t] * x.delta - (double)sD[t + 1]);
-                    xs[t] = (float)x.m01;
+                    rho0[t] = ff_dot2_minus(sb0[t], x.m00, sb1[t], x.m10, sb0[t + 1]);
+                    rho1[t] = ff_dot2_minus(sb0[t], x.m01, sb1[t], ff_from(1.0f), sb1[t + 1]);
+                    rhoD[t] = ff_dot2_minus(sD[t], x.delta, 0.0f, ff_from(0.0f), sD[t + 1]);
+                    xs[t] = ff_round(x.m01);
                     const Xfer xf = xfer(rr[t], A.a2, A.mode);
                     const float n0 = fmaf(c0, xf.m00, fmaf(c1, xf.m10, rho0[t]));
                     c1 = fmaf(c0, xf.m01, c1 + rho1[t]);
