@@ -422,7 +422,7 @@ def run_next_rows(torch, B, vol, vol_d, poses_d, fans, prm, sched, G, flush, str
 def run_scale_form(torch, flush, stream, steps, warmup, with_err=True):
     """Precision + scale workload: 512^3 BF16 volume at 0.5 mm, 64 hemisphere
     poses x 1024 rays x 4096 samples at 0.05 mm, 7 MHz, forward+backward,
-    with and without the FP64-residual refinement pass."""
+    with and without the refinement pass (double-single residuals)."""
     from paper_2508_06768_gb300.render import BatchRenderer
     dev = torch.device("cuda", torch.cuda.current_device())
     v5 = I.fine_brain_phantom(512, 0.5, seed=5)
@@ -444,7 +444,7 @@ def run_scale_form(torch, flush, stream, steps, warmup, with_err=True):
         out[key] = {"value": total5 / (ms * 1e-3), "ms": ms, "ray_samples": total5,
                     "rays_with_pole": int(st[0]), "rays_refined": int(st[3]), "rays": 64 * 1024,
                     "workload": "512^3 BF16 at 0.5 mm, 64 poses x 1024 rays x 4096 samples at 0.05 mm, 7 MHz, "
-                                "literal |R|, speckle+blur%s" % (", FP64-residual refinement" if refine else "")}
+                                "literal |R|, speckle+blur%s" % (", refinement pass" if refine else "")}
         if refine and with_err:
             out[key]["err_vs_fp64"] = scale_errors(torch, v5, vb, poses5, fans5, prm5)
         del g, r5

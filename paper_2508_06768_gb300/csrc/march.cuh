@@ -27,7 +27,7 @@ struct MarchArgs {
     VolGeo g;
     float a2;         // a^2 inside the depth systems (1 with the depth-gain reading)
     int mode;
-    double a2d;       // the same in FP64 (residual of the refinement pass)
+    double a2d;       // the same in FP64 (converted to double-single by the refinement pass)
     int atten;        // 1: depth-gain reading (lossless systems; the gain is a separate row pass)
     Speckle sp;
 };

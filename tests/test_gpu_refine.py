@@ -1,6 +1,6 @@
 """The precision form with one refinement pass: the FP32 depth recurrence is
-kept, its residuals are taken in FP64 and the error recurrence is solved in
-FP32.  Checked against the FP64 oracle on short rays (FP32 volume) and on
+kept, its residuals are taken in double-single arithmetic (FP64-class
+precision on the FP32 pipes) and the error recurrence is solved in FP32.  Checked against the FP64 oracle on short rays (FP32 volume) and on
 long S = 4096 rays of a BF16 volume (against the oracle run on the
 BF16-rounded volume), next to the unrefined path, and batched against
 single-pose bitwise."""
@@ -75,8 +75,8 @@ def _near_pole_err(img, ref, first, det, S, W, blur):
 def test_refine_holds_near_pole_rows(case):
     # Eq. 4's depth systems of the literal model of Eq. 1 pass through poles
     # (det(A_k) -> 0); echo rows next to one amplify rounding by ~1/det.  The
-    # refined pass takes its residuals against FP64 samples of the FP64 ray
-    # positions, so the refined rows with det in [1e-6, COND_DET) also meet
+    # refined pass takes its residuals against double-single samples at the
+    # FP64 ray line's positions, so the refined rows with det in [1e-6, COND_DET) also meet
     # the FP32 tolerance, without the det weighting the unrefined path needs.
     if case == "small_literal":
         vol, pose, fan, prm = I.workload_small()

@@ -1,7 +1,7 @@
 """Precision + scale workload: a 512^3 BF16 volume at 0.5 mm (brain recipe
 upsampled, plus fine texture), 64 hemisphere poses x 1024 rays x 4096
 samples at 0.05 mm, 7 MHz, rendered forward+backward in one batched call
-with the FP64-residual refinement pass.  Four seeded poses are compared with
+with the refinement pass (double-single residuals).  Four seeded poses are compared with
 the FP64 oracle on the BF16-rounded volume, on a block of 16 rays each:
 images, and the pose and volume gradients of a loss weighting only those
 blocks."""
