@@ -55,7 +55,15 @@ __global__ void k_ray_runs(const RayGeo *__restrict__ geo, const long long *__re
             runs[slot] = run;
             keys[slot] = brick;
             vals[slot] = (uint32_t)slot;
-            atomicAdd(brick_work + brick, (unsigned long long)run.len);   // for the unit order only
+            {   // for the unit order only: lanes on the same brick add once, through
+                // their lowest lane (integer sums, so the order does not matter)
+                const unsigned act = __activemask();
+                const unsigned grp = __match_any_sync(act, brick);
+                unsigned long long sum = 0;
+                for (unsigned m = grp; m; m &= m - 1)
+                    sum += (unsigned long long)__shfl_sync(grp, run.len, __ffs(m) - 1);
+                if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(brick_work + brick, sum);
+            }
             cnt++;
         } else if (status) {
             atomicOr(status + 2, (uint32_t)DIFFUS_STATUS_QUEUE);
