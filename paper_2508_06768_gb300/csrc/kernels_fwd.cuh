@@ -283,6 +283,30 @@ __device__ void blur_strip(const float *__restrict__ in, float *__restrict__ out
 #pragma unroll
         for (int t = 0; t < 2 * WW; t++) win[t] = ld(j0 + t - WW);
         for (int jb = j0; jb < j1; jb += B) {
+            // a block whose rays all have the full window inside the fan (the
+            // same for every lane): no edge guards and the interior norm;
+            // the other lanes' rows of this block are read at row 0 (valid
+            // memory) and not written
+            if (jb >= WW && jb + B + 2 * WW <= n && jb + B <= j1) {
+                const float *p = src + (size_t)(jb + WW) * S;
+                float *q = dst + (size_t)jb * S;
+#pragma unroll
+                for (int t = 0; t < B; t++) {
+                    const float x = __ldg(p + (size_t)t * S);
+                    win[2 * WW + t] = TRANSPOSE ? x * rfull : x;
+                }
+#pragma unroll
+                for (int i = 0; i < B; i++) {
+                    float acc = w[0] * win[i + WW];
+#pragma unroll
+                    for (int m = 1; m <= WW; m++) acc = fmaf(w[m], win[i + WW - m] + win[i + WW + m], acc);
+                    if (!TRANSPOSE) acc *= rfull;
+                    if (kin) q[(size_t)i * S] = acc * gk;
+                }
+#pragma unroll
+                for (int t = 0; t < 2 * WW; t++) win[t] = win[t + B];
+                continue;
+            }
             float nx[B];
 #pragma unroll
             for (int t = 0; t < B; t++) nx[t] = (kin && jb + WW + t < n) ? __ldg(src + (size_t)(jb + WW + t) * S) : 0.0f;
