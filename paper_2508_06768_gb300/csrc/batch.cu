@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kTileWarpsBwd * 32, kBwdValThreadsPerSM / (kTi
 }
 
 // Speckle factors of the whole batch ahead of the one-warp-per-ray forward:
-// one warp per (tile, 64-row block) item.
+// one warp per (tile, kSpkRows-row block) item.
 __global__ void __launch_bounds__(kTileWarps * 32) k_batch_speckle(Speckle sp, const TileDesc *__restrict__ tiles,
                                                                    const SpkItem *__restrict__ items, int64_t n_items,
                                                                    float *__restrict__ mbuf)

@@ -217,10 +217,13 @@ namespace dfs {
 
 // ------------------------------------------------ speckle field, ahead of the march
 
-constexpr int kSpkRows = 64;   // rows of one speckle work item
+// rows of one speckle work item: 32 keep the staging at 4.2 KB per warp, so
+// that 8 CTAs of 4 warps fit an SM (forward phase on the 512-pose batch
+// 1.847 ms with 64-row items, 1.777 with 32)
+constexpr int kSpkRows = 32;
 constexpr int kSpkLd = kSpkRows + 1;
 
-// A speckle work item: rows k0 .. k0+63 of the rays of one forward tile.
+// A speckle work item: rows k0 .. k0+kSpkRows-1 of the rays of one forward tile.
 struct SpkItem {
     int32_t tile, k0;
 };
@@ -308,7 +311,7 @@ __device__ void speckle_item(const Speckle &sp, const TileDesc &tl, int k0, floa
         }
     }
     __syncwarp();
-    // one ray's 64 rows per pair of store instructions
+    // one ray's rows of the item per store instruction
     for (int rr = 0; rr < cnt; rr++) {
         float *dst = mbuf + tl.row0 + (int64_t)rr * S + k0;
         for (int e = lane; e < n; e += kWarp) __stcs(dst + e, sm.m[rr * kSpkLd + e]);
