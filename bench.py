@@ -687,7 +687,7 @@ def run_native(args):
         # form 0 runs the marches with one warp per ray, form 1 with one lane
         # per ray (grids of 4-warp CTAs sized from warps x CTAs)
         sched, _ = autotune(vol_d, vol.spacing, vol.origin, fans, prm, poses_d, G,
-                            candidates=[(8, 3, 8, 0), (8, 2, 8, 0), (8, 3, 16, 0), (4, 6, 8, 0), (4, 3, 8, 1)],
+                            candidates=[(4, 7, 8, 0), (4, 7, 16, 0), (8, 3, 8, 0), (4, 6, 8, 0), (4, 3, 8, 1)],
                             reps=1)
     r = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm, schedule=sched, with_bwd=True, pose_ctr=pose0)
 

@@ -214,8 +214,8 @@ int diffus_render_fwd_noalloc(const void *vol, const diffus_volume_desc *vd, con
  * of the march), 1 one lane per ray over tiles of 32 consecutive rays of a
  * pose (the rays' depth recurrences run side by side).  Zero fields of
  * the first three take defaults: 4 warps per CTA, as many CTAs per SM as
- * fill 768 threads (the marches' register budget: 6 with 4 warps), and 8
- * gather CTAs per SM.  bwd_chunks (0 or 1: one chunk; at most
+ * fill 896 threads (the forward march's register budget: 7 with 4 warps),
+ * and 8 gather CTAs per SM.  bwd_chunks (0 or 1: one chunk; at most
  * DIFFUS_MAX_BWD_CHUNKS): the poses are split into that many contiguous
  * ranges of about equal work (diffus_batch_plan_chunks returns them), and
  * the backward runs range by range (blur transpose, then adjoint march of

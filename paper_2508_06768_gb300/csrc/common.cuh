@@ -23,7 +23,11 @@ constexpr int kSegPad = kSeg + kSeg / kChunk;  // padded smem row (conflict-free
 // at <= 85.
 constexpr int kBwdThreadsPerSM = 512;
 constexpr int kBwdValThreadsPerSM = 768;
-constexpr int kFwdThreadsPerSM = 768;
+// resident threads per SM the forward marches are compiled for: 896 holds
+// the 4-warp forward at 72 registers with 7 CTAs per SM (measured on the
+// 512-pose batch: forward phase 1.780 ms at 768 threads, 1.711 at 896, 1.789
+// at 1024 and 64 registers)
+constexpr int kFwdThreadsPerSM = 896;
 constexpr float kPoleEps = 1e-6f;            // det(A_k) threshold of a well-posed depth
 constexpr int kMaxW = 32;                    // largest lateral blur half-width
 
