@@ -141,10 +141,10 @@ BOUND = {"march_fwd": "alu", "march_bwd": "alu", "gather_units": "alu", "blur": 
 # dram__bytes_write.sum of one launch over the first 192 poses of the
 # workload, the forward phase being the speckle kernel plus the march,
 # divided by its ray-samples); absent where the kernel changed since.
-NCU_DRAM_PER_UNIT = {"blur": 7.42, "blur_T": 7.43, "gather_units": 8.53}
+NCU_DRAM_PER_UNIT = {"blur": 7.44, "blur_T": 7.44, "gather_units": 8.54}
 # the marches' figures depend on the forward form (fwd_form 0: one warp per
 # ray; 1: one lane per ray), set from the capture of that form
-NCU_DRAM_PER_UNIT_FORM = {0: {"march_fwd": 18.84, "march_bwd": 19.69}, 1: {"march_fwd": 25.77, "march_bwd": 21.51}}
+NCU_DRAM_PER_UNIT_FORM = {0: {"march_fwd": 18.86, "march_bwd": 19.69}, 1: {"march_fwd": 25.77, "march_bwd": 21.51}}
 
 
 def median_pose_order(fans):
