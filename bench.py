@@ -756,10 +756,12 @@ def run_native(args):
     # ---- end to end through the public API: host buffers, copies inside the timed region.
     # The step pipelines its transfers the way a user of the API can: the
     # volume and poses go up first, dL/dimage goes up on a second stream in
-    # the plan's backward chunks while the forward marches (each chunk's event
+    # the plan's pose chunks while the forward marches (each chunk's event
     # releases that chunk's blur transpose and adjoint march), and the images
     # come down on a third stream from the forward's end event while the
-    # backward runs; the gradients come down last.
+    # backward runs (downloading each chunk's images as soon as it is rendered
+    # measured slower: the early download slows the uploads the backward
+    # waits for); the gradients come down last.
     e2e = None
     if not args.no_e2e:
         n_chunks = 4   # measured: 4 ranges 6.85 ms, 8 ranges 7.14, one 7.53 (each range's launches end on a tail)
@@ -843,6 +845,49 @@ def run_native(args):
                        "runs" % len(ranges),
                "link": link}
         del r_e2e
+        # forward only through the same API (the serving form): volume and
+        # poses up, images down, each pose range's images as soon as the
+        # forward has finished them (diffus_trace.fwd_chunk_done)
+        n_fc = 8
+        r_f = BatchRenderer(vol_d, vol.spacing, vol.origin, fans, prm, with_bwd=False, pose_ctr=pose0,
+                            schedule=B.ScheduleDesc(s5.rays_per_cta, s5.ctas_per_sm, s5.brick, s5.fwd_form, n_fc))
+        franges = r_f.chunk_ranges()
+        ev_f = [torch.cuda.Event() for _ in franges]
+        for e in ev_f:
+            e.record(stream)
+        trf = B.TraceDesc()
+        for c, e in enumerate(ev_f):
+            trf.fwd_chunk_done[c] = e.cuda_event
+        f_ms = []
+        for it in range(n_e2e + 1):
+            flush.zero_()
+            torch.cuda._sleep(HOST_SLACK_CYCLES)
+            e0.record(stream)
+            vol_d.copy_(vol_h, non_blocking=True)
+            poses_d.copy_(poses_h, non_blocking=True)
+            r_f.run(poses_d, stream=stream, trace=trf)
+            for (a, b), e in zip(franges, ev_f):
+                down.wait_event(e)
+                with torch.cuda.stream(down):
+                    img_h[a:b].copy_(r_f.images[a:b], non_blocking=True)
+            stream.wait_stream(down)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it > 0:
+                f_ms.append(e0.elapsed_time(e1))
+        fo_ms = float(np.mean(f_ms))
+        if ws > 1:
+            t = torch.tensor([fo_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            fo_ms = float(t.item())
+        e2e["forward_only"] = {"value": job_units / (fo_ms * 1e-3), "unit": UNIT,
+                               "ms_per_step": fo_ms,
+                               "ms_min_median_max": [float(np.min(f_ms)), float(np.median(f_ms)), float(np.max(f_ms))],
+                               "h2d_bytes_per_step": int(vol_h.numel() * 4 + poses_h.numel() * 4),
+                               "d2h_bytes_per_step": int(img_h.numel() * 4),
+                               "form": "forward only, one diffus_render_batch call per step in %d pose ranges, each "
+                                       "range's images downloaded once rendered" % len(franges)}
+        del r_f
     clk.__enter__()
 
     # ---- forms: batched vs the plain single-pose kernel, forward only, speckle off, BF16

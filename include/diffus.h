@@ -215,25 +215,29 @@ int diffus_render_fwd_noalloc(const void *vol, const diffus_volume_desc *vd, con
  * pose (the rays' depth recurrences run side by side).  Zero fields of
  * the first three take defaults: 4 warps per CTA, as many CTAs per SM as
  * fill 896 threads (the forward march's register budget: 7 with 4 warps),
- * and 8 gather CTAs per SM.  bwd_chunks (0 or 1: one chunk; at most
- * DIFFUS_MAX_BWD_CHUNKS): the poses are split into that many contiguous
- * ranges of about equal work (diffus_batch_plan_chunks returns them), and
- * the backward runs range by range (blur transpose, then adjoint march of
- * the range's rays), each after its own wait event (diffus_trace.wait_chunk),
- * so the backward can start on the first poses' dL/dimage while the rest is
- * still being uploaded.  The forward-only one-lane-per-ray backward runs as
- * one range after all events.  rays_per_cta, ctas_per_sm, brick and
- * bwd_chunks change launch shapes and order only, never the arithmetic of a
- * ray or a brick (results are bitwise the same); the two forward forms order
- * the FP32 arithmetic of a ray differently, so their images agree to
- * rounding, not bitwise. */
-#define DIFFUS_MAX_BWD_CHUNKS 16
+ * and 8 gather CTAs per SM.  chunks (0 or 1: one chunk; at most
+ * DIFFUS_MAX_CHUNKS): the poses are split into that many contiguous
+ * ranges of about equal work (diffus_batch_plan_chunks returns them), for
+ * callers whose images and dL/dimage travel to and from the host.  The
+ * backward runs range by range (blur transpose, then adjoint march of the
+ * range's rays), each after its own wait event (diffus_trace.wait_chunk),
+ * so it can start on the first poses' dL/dimage while the rest is still
+ * being uploaded; the one-lane-per-ray backward and the depth-gain row
+ * pass without blur run as one range after all events.  When the call's
+ * trace asks for diffus_trace.fwd_chunk_done events, with fwd_form 0 and
+ * refine = 0 the forward also runs range by range (march, then blur of the
+ * range) and records fwd_chunk_done[c] once range c's images are final, so
+ * their download can start while later ranges render.  rays_per_cta, ctas_per_sm, brick and chunks change launch
+ * shapes and order only, never the arithmetic of a ray or a brick (results
+ * are bitwise the same); the two forward forms order the FP32 arithmetic of
+ * a ray differently, so their images agree to rounding, not bitwise. */
+#define DIFFUS_MAX_CHUNKS 16
 typedef struct {
     int32_t rays_per_cta;
     int32_t ctas_per_sm;
     int32_t brick;
     int32_t fwd_form;
-    int32_t bwd_chunks;
+    int32_t chunks;
 } diffus_schedule;
 
 /* Optional tracing of the batched call: when non-NULL, the library records
@@ -262,12 +266,19 @@ typedef struct {
      * march; the forward's outputs can likewise be downloaded from the
      * DIFFUS_TR_FWD_END event on while the backward runs. */
     void *wait_before_bwd;
-    /* Optional inputs of a plan with bwd_chunks > 1: the stream waits on
+    /* Optional inputs of a plan with chunks > 1: the stream waits on
      * wait_chunk[c] (a cudaEvent_t, or NULL) before the backward of pose
      * range c, so a caller that uploads dL/dimage range by range records
      * event c after range c's copy.  Entries at and past the plan's chunk
      * count are ignored. */
-    void *wait_chunk[DIFFUS_MAX_BWD_CHUNKS];
+    void *wait_chunk[DIFFUS_MAX_CHUNKS];
+    /* Optional outputs (cudaEvent_t, or NULL), one per pose range of the
+     * plan: recorded on the call's stream once range c's images are final.
+     * Any non-NULL entry makes the forward run range by range where it can
+     * (diffus_schedule.chunks), each event after its range's march and blur;
+     * otherwise all are recorded after the whole forward.  Entries at and
+     * past the plan's chunk count are ignored. */
+    void *fwd_chunk_done[DIFFUS_MAX_CHUNKS];
 } diffus_trace;
 
 /* Size of the plan blob for P fans (host). */
@@ -285,7 +296,7 @@ int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan *fans, int3
                       const diffus_params *prm, const diffus_schedule *sched, void *plan_host,
                       size_t plan_bytes, int64_t *img_offsets, size_t *ws_fwd, size_t *ws_bwd);
 
-/* Pose ranges of the backward chunks of a plan (host): writes the first
+/* Pose ranges of the chunks of a plan (host): writes the first
  * pose of each chunk and, last, P into first_pose (host int32[n + 1], n the
  * chunk count) and returns n (>= 1), or a negative error code (DIFFUS_E_NULL,
  * DIFFUS_E_PLAN for a buffer that is not a plan, DIFFUS_E_WORKSPACE when

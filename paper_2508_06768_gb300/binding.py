@@ -40,12 +40,12 @@ class ParamsDesc(C.Structure):
                 ("atten", C.c_int32)]
 
 
-MAX_BWD_CHUNKS = 16
+MAX_CHUNKS = 16
 
 
 class ScheduleDesc(C.Structure):
     _fields_ = [("rays_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32), ("brick", C.c_int32),
-                ("fwd_form", C.c_int32), ("bwd_chunks", C.c_int32)]
+                ("fwd_form", C.c_int32), ("chunks", C.c_int32)]
 
 
 class ScanGridDesc(C.Structure):
@@ -55,7 +55,7 @@ class ScanGridDesc(C.Structure):
 
 class TraceDesc(C.Structure):
     _fields_ = [("event", C.c_void_p * 10), ("wait_before_bwd", C.c_void_p),
-                ("wait_chunk", C.c_void_p * MAX_BWD_CHUNKS)]
+                ("wait_chunk", C.c_void_p * MAX_CHUNKS), ("fwd_chunk_done", C.c_void_p * MAX_CHUNKS)]
 
 
 class DiffusError(RuntimeError):
@@ -251,12 +251,12 @@ def batch_plan(vol, spacing, origin, fans, params, schedule=None):
 
 
 def batch_plan_chunks(plan_host):
-    """diffus_batch_plan_chunks (host): the first pose of every backward
-    chunk of a plan, then P (int32 numpy [n + 1])."""
+    """diffus_batch_plan_chunks (host): the first pose of every pose chunk
+    of a plan, then P (int32 numpy [n + 1])."""
     lib = load()
-    out = np.zeros(MAX_BWD_CHUNKS + 1, dtype=np.int32)
+    out = np.zeros(MAX_CHUNKS + 1, dtype=np.int32)
     n = lib.diffus_batch_plan_chunks(C.c_void_p(plan_host.data_ptr()), out.ctypes.data_as(C.POINTER(C.c_int32)),
-                                     MAX_BWD_CHUNKS + 1)
+                                     MAX_CHUNKS + 1)
     _check(min(n, 0), "diffus_batch_plan_chunks")
     return out[:n + 1].copy()
 

@@ -53,8 +53,8 @@ struct PlanHeader {
     // queue entries chunk_q[c] .. chunk_q[c+1]-1 of the ray order and blur
     // strips chunk_t[c] .. chunk_t[c+1]-1 (both lists are chunk-major)
     int32_t n_chunks, pad_chunks;
-    int32_t chunk_pose[DIFFUS_MAX_BWD_CHUNKS + 1];
-    int64_t chunk_q[DIFFUS_MAX_BWD_CHUNKS + 1], chunk_t[DIFFUS_MAX_BWD_CHUNKS + 1];
+    int32_t chunk_pose[DIFFUS_MAX_CHUNKS + 1];
+    int64_t chunk_q[DIFFUS_MAX_CHUNKS + 1], chunk_t[DIFFUS_MAX_CHUNKS + 1];
 };
 
 template <typename T>
@@ -131,10 +131,10 @@ int64_t count_spk(const diffus_fan *fans, int P)
 }
 
 // Work-queue counters of one call: 0 forward march, 1 adjoint, 2 blur,
-// 3 blur transpose, 4-5 refinement list and tickets, 6-7 spare, then two per
-// backward chunk (blur transpose, adjoint).
+// 3 blur transpose, 4-5 refinement list and tickets, 6-7 spare, then four
+// per pose chunk (forward march, blur, blur transpose, adjoint).
 constexpr int kCtrChunk = 8;
-constexpr int kCounters = kCtrChunk + 2 * DIFFUS_MAX_BWD_CHUNKS;
+constexpr int kCounters = kCtrChunk + 4 * DIFFUS_MAX_CHUNKS;
 
 struct BatchLayout {
     RayGeo *geo;
@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(WARPS * 32, kFwdThreadsPerSM / (WARPS * 32)) k
                                                           int *__restrict__ valid, uint32_t *__restrict__ status,
                                                           unsigned *__restrict__ counter, float4 *__restrict__ ckpt,
                                                           float *__restrict__ mbuf, float2 *__restrict__ kbuf,
-                                                          const float *__restrict__ spk_in, RefineSel sel)
+                                                          const float *__restrict__ spk_in, RefineSel sel, int64_t q0,
+                                                          int64_t qn)
 {
     __shared__ float buf[WARPS][kSegPad];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -233,8 +234,8 @@ __global__ void __launch_bounds__(WARPS * 32, kFwdThreadsPerSM / (WARPS * 32)) k
         unsigned q = 0;
         if (lane == 0) q = atomicAdd(counter, 1u);
         q = __shfl_sync(0xffffffffu, q, 0);
-        if ((int64_t)q >= B.total_rays) break;
-        const int r = B.order[q];
+        if ((int64_t)q >= qn) break;   // entries q0 .. q0+qn-1 of the ray order
+        const int r = B.order[q0 + q];
         RayGeo rg = geo[r];
         MarchArgs Ap = A;
         if (!A.atten) {   // the depth-gain reading keeps a2 = 1 (lossless systems)
@@ -460,7 +461,7 @@ struct FwdLaunch {
 template <typename T, int WARPS>
 void launch_fwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out, int *valid,
                   uint32_t *status, unsigned *counter, const FwdKeep &kp, const FwdLaunch &fl, const RefineSel &sel,
-                  const PoseFrame *frames, const VolPlace &vp, cudaStream_t s)
+                  const PoseFrame *frames, const VolPlace &vp, int64_t q0, int64_t qn, cudaStream_t s)
 {
     if (fl.form == 1)
         k_batch_fwd_tiles<T><<<fl.grid, kTileWarps * 32, 0, s>>>((const T *)vol, A, B, geo, fl.tiles, fl.n_tiles,
@@ -468,7 +469,7 @@ void launch_fwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const 
                                                                  kp.kbuf, kp.bcar, sel);
     else
         k_batch_fwd<T, WARPS><<<fl.grid, WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, out, valid, status, counter,
-                                                             kp.ckpt, kp.mbuf, kp.kbuf, fl.spk_in, sel);
+                                                             kp.ckpt, kp.mbuf, kp.kbuf, fl.spk_in, sel, q0, qn);
     if (sel.rinfo)
         k_batch_refine<T, WARPS><<<kRefineWarpsPerSM / WARPS * sm_count(), WARPS * 32, 0, s>>>((const T *)vol, A, B, geo, frames, vp, out, valid,
                                                                   status, kp.ckpt, sel);
@@ -514,12 +515,13 @@ int launch_bwd_t(const void *vol, const MarchArgs &A, const BatchDev &B, const R
 template <typename T>
 int launch_fwd_w(int warps, const void *vol, const MarchArgs &A, const BatchDev &B, const RayGeo *geo, float *out,
                  int *valid, uint32_t *status, unsigned *counter, const FwdKeep &kp, const FwdLaunch &fl,
-                 const RefineSel &sel, const PoseFrame *frames, const VolPlace &vp, cudaStream_t s)
+                 const RefineSel &sel, const PoseFrame *frames, const VolPlace &vp, int64_t q0, int64_t qn,
+                 cudaStream_t s)
 {
     switch (warps) {
-    case 2: launch_fwd_t<T, 2>(vol, A, B, geo, out, valid, status, counter, kp, fl, sel, frames, vp, s); break;
-    case 4: launch_fwd_t<T, 4>(vol, A, B, geo, out, valid, status, counter, kp, fl, sel, frames, vp, s); break;
-    case 8: launch_fwd_t<T, 8>(vol, A, B, geo, out, valid, status, counter, kp, fl, sel, frames, vp, s); break;
+    case 2: launch_fwd_t<T, 2>(vol, A, B, geo, out, valid, status, counter, kp, fl, sel, frames, vp, q0, qn, s); break;
+    case 4: launch_fwd_t<T, 4>(vol, A, B, geo, out, valid, status, counter, kp, fl, sel, frames, vp, q0, qn, s); break;
+    case 8: launch_fwd_t<T, 8>(vol, A, B, geo, out, valid, status, counter, kp, fl, sel, frames, vp, q0, qn, s); break;
     default: return DIFFUS_E_PLAN;
     }
     return DIFFUS_OK;
@@ -612,7 +614,7 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     if (sc.brick == 0) sc.brick = 8;    // gather CTAs per SM
     if (sc.rays_per_cta != 2 && sc.rays_per_cta != 4 && sc.rays_per_cta != 8) return DIFFUS_E_PARAM;
     if (sc.ctas_per_sm < 1 || sc.ctas_per_sm > 32 || sc.brick < 1 || sc.brick > 64) return DIFFUS_E_PARAM;
-    if (sc.bwd_chunks < 0 || sc.bwd_chunks > DIFFUS_MAX_BWD_CHUNKS) return DIFFUS_E_PARAM;
+    if (sc.chunks < 0 || sc.chunks > DIFFUS_MAX_CHUNKS) return DIFFUS_E_PARAM;
 
     memset(plan_host, 0, (size_t)z.bytes);
     PlanHeader &H = *(PlanHeader *)plan_host;
@@ -646,7 +648,7 @@ extern "C" int diffus_batch_plan(const diffus_volume_desc *vd, const diffus_fan 
     {
         // backward chunks: contiguous pose ranges cut where the running work
         // (ray-samples) first reaches c/n of the total, each range non-empty
-        const int n = std::max(1, std::min<int>(sc.bwd_chunks, P));
+        const int n = std::max(1, std::min<int>(sc.chunks, P));
         std::vector<double> cum((size_t)P + 1, 0.0);
         for (int p = 0; p < P; p++) cum[p + 1] = cum[p] + (double)fans[p].n_rays * (double)fans[p].n_samples;
         H.n_chunks = n;
@@ -755,7 +757,7 @@ extern "C" int diffus_batch_plan_chunks(const void *plan_host, int32_t *first_po
 {
     if (!plan_host || !first_pose) return DIFFUS_E_NULL;
     const PlanHeader &H = *(const PlanHeader *)plan_host;
-    if (H.magic != kPlanMagic || H.n_chunks < 1 || H.n_chunks > DIFFUS_MAX_BWD_CHUNKS) return DIFFUS_E_PLAN;
+    if (H.magic != kPlanMagic || H.n_chunks < 1 || H.n_chunks > DIFFUS_MAX_CHUNKS) return DIFFUS_E_PLAN;
     if (max_entries < H.n_chunks + 1) return DIFFUS_E_WORKSPACE;
     for (int c = 0; c <= H.n_chunks; c++) first_pose[c] = H.chunk_pose[c];
     return H.n_chunks;
@@ -831,23 +833,54 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
         fl.spk_in = L.mbuf;
     }
     if (H.fwd_form == 1) fl.grid = sm_count() * std::max(1, H.ctas_per_sm * H.warps / kTileWarps);
-    if (vd->dtype == DIFFUS_F32)
-        rc = launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0, kp, fl,
-                                 L.sel, L.frames, vp, s);
-    else
-        rc = launch_fwd_w<unsigned short>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, L.counter + 0,
-                                          kp, fl, L.sel, L.frames, vp, s);
-    if (rc) return rc;
+    auto march = [&](int64_t q0, int64_t qn, unsigned *ctr) {
+        if (vd->dtype == DIFFUS_F32)
+            return launch_fwd_w<float>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, ctr, kp, fl, L.sel,
+                                       L.frames, vp, q0, qn, s);
+        return launch_fwd_w<unsigned short>(H.warps, vol, A, B, L.geo, march_out, ray_valid, status, ctr, kp, fl,
+                                            L.sel, L.frames, vp, q0, qn, s);
+    };
     const int rgrid = (int)std::min<int64_t>((H.total_rays + 7) / 8, (int64_t)sm_count() * 16);
-    // the depth gain rides on the blur's output; without blur it is a row pass
-    if (prm->atten && !prm->blur) k_batch_row_gain<<<rgrid, 256, 0, s>>>(march_out, march_out, B);
-    mark(DIFFUS_TR_BLUR);
     BlurArgs bl{(float)prm->sigma0, (float)prm->sigma1, H.blurW, prm->atten};
     const int tgrid = (int)std::min<int64_t>((H.n_tiles + kBlurWarps - 1) / kBlurWarps, (int64_t)sm_count() * 16);
     const PlanPose *dpose = at<PlanPose>(plan_dev, H.off_pose);
     const BlurTile *dtiles = at<BlurTile>(plan_dev, H.off_tiles);
-    if (prm->blur) launch_batch_blur<false>(L.y, images, dpose, dtiles, H.n_tiles, bl, tgrid, L.counter + 2, s);
-    mark(DIFFUS_TR_FWD_END);
+    auto chunk_done = [&](int c) {
+        if (trace && c < DIFFUS_MAX_CHUNKS) record_mark((cudaEvent_t)trace->fwd_chunk_done[c], external, s);
+    };
+    // the forward range by range (march, then blur of the range) when the
+    // caller asks for per-range events, so that a range's images can leave
+    // while later ranges render (each range's launches end on a tail, so a
+    // caller that does not download early is better served whole); the
+    // refined pass and the depth-gain row pass need the whole batch
+    bool want_ranges = false;
+    for (int c = 0; trace && c < H.n_chunks && c < DIFFUS_MAX_CHUNKS; c++) want_ranges |= trace->fwd_chunk_done[c] != nullptr;
+    const bool fwd_chunked = want_ranges && H.n_chunks > 1 && H.fwd_form == 0 && !prm->refine &&
+                             !(prm->atten && !prm->blur);
+    if (fwd_chunked) {
+        for (int c = 0; c < H.n_chunks; c++) {
+            const int64_t q0 = H.chunk_q[c], qn = H.chunk_q[c + 1] - q0;
+            if (qn > 0 && (rc = march(q0, qn, L.counter + kCtrChunk + 4 * c))) return rc;
+            if (c == H.n_chunks - 1) mark(DIFFUS_TR_BLUR);
+            const int64_t t0 = H.chunk_t[c], tn = H.chunk_t[c + 1] - t0;
+            if (prm->blur && tn > 0) {
+                const int cgrid = (int)std::max<int64_t>(1, std::min<int64_t>((tn + kBlurWarps - 1) / kBlurWarps,
+                                                                              (int64_t)sm_count() * 16));
+                launch_batch_blur<false>(L.y, images, dpose, dtiles + t0, tn, bl, cgrid,
+                                         L.counter + kCtrChunk + 4 * c + 1, s);
+            }
+            chunk_done(c);
+        }
+        mark(DIFFUS_TR_FWD_END);
+    } else {
+        if ((rc = march(0, H.total_rays, L.counter + 0))) return rc;
+        // the depth gain rides on the blur's output; without blur it is a row pass
+        if (prm->atten && !prm->blur) k_batch_row_gain<<<rgrid, 256, 0, s>>>(march_out, march_out, B);
+        mark(DIFFUS_TR_BLUR);
+        if (prm->blur) launch_batch_blur<false>(L.y, images, dpose, dtiles, H.n_tiles, bl, tgrid, L.counter + 2, s);
+        mark(DIFFUS_TR_FWD_END);
+        for (int c = 0; c < H.n_chunks; c++) chunk_done(c);
+    }
     if ((rc = launch_status())) return rc;
     if (!bwd) return DIFFUS_OK;
     if (trace && trace->wait_before_bwd &&
@@ -858,7 +891,7 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
         (grad_poses && ((uintptr_t)grad_poses) % 4))
         return DIFFUS_E_ALIGN;
     auto wait_chunk = [&](int c) {
-        if (trace && c < DIFFUS_MAX_BWD_CHUNKS && trace->wait_chunk[c] &&
+        if (trace && c < DIFFUS_MAX_CHUNKS && trace->wait_chunk[c] &&
             cudaStreamWaitEvent(s, (cudaEvent_t)trace->wait_chunk[c], 0) != cudaSuccess)
             return DIFFUS_E_LAUNCH;
         return DIFFUS_OK;
@@ -884,12 +917,12 @@ extern "C" int diffus_render_batch(const void *vol, const diffus_volume_desc *vd
                                                                               (int64_t)sm_count() * 16));
                 if (tn > 0)
                     launch_batch_blur<true>(grad_images, L.gy, dpose, dtiles + t0, tn, bl, cgrid,
-                                            L.counter + kCtrChunk + 2 * c, s);
+                                            L.counter + kCtrChunk + 4 * c + 2, s);
                 gyc = L.gy;
             }
             if (c == 0) mark(DIFFUS_TR_MARCH_BWD);
             const int64_t q0 = H.chunk_q[c], qn = H.chunk_q[c + 1] - q0;
-            if (qn > 0 && (rc = adjoint(gyc, q0, qn, L.counter + kCtrChunk + 2 * c + 1))) return rc;
+            if (qn > 0 && (rc = adjoint(gyc, q0, qn, L.counter + kCtrChunk + 4 * c + 3))) return rc;
         }
         rc = DIFFUS_OK;
     } else {

@@ -43,17 +43,29 @@ def _gauss(sigma, device):
     return w / w.sum()
 
 
+def _smooth(e, k, dim):
+    """Zero-padded correlation of a 2D tensor with the odd-length weights k
+    along dim, as a fixed-order sum of shifted copies: deterministic in the
+    forward and in its gradient (a library convolution's gradient may
+    accumulate in a different order from run to run)."""
+    r = k.numel() // 2
+    n = e.shape[dim]
+    ep = torch.nn.functional.pad(e, (r, r) if dim == 1 else (0, 0, r, r))
+    out = k[0] * ep.narrow(dim, 0, n)
+    for i in range(1, k.numel()):
+        out = out + k[i] * ep.narrow(dim, i, n)
+    return out
+
+
 def envelope(img, tau, sigma_rows=3.0, sigma_rays=1.0):
     """Smoothed log envelope G * log(1 + |img| / tau) of [n_rays][S] images
     (zero padding at the borders)."""
-    e = torch.log1p(img.abs() / tau)[None, None]
+    e = torch.log1p(img.abs() / tau)
     if sigma_rows > 0:
-        k = _gauss(sigma_rows, img.device)
-        e = torch.nn.functional.conv2d(e, k.view(1, 1, 1, -1), padding=(0, k.numel() // 2))
+        e = _smooth(e, _gauss(sigma_rows, img.device), 1)
     if sigma_rays > 0:
-        k = _gauss(sigma_rays, img.device)
-        e = torch.nn.functional.conv2d(e, k.view(1, 1, -1, 1), padding=(k.numel() // 2, 0))
-    return e[0, 0]
+        e = _smooth(e, _gauss(sigma_rays, img.device), 0)
+    return e
 
 
 def register_pose(volume: torch.Tensor, target: torch.Tensor, fan, params, pose0, spacing=(1.0, 1.0, 1.0),

@@ -64,7 +64,7 @@ class BatchRenderer:
         dev = volume.device
         plan, offs, wsf, wsb = B.batch_plan(self.volume, spacing, origin, self.fans, params, schedule)
         # first pose of every backward chunk, then P (one chunk unless the
-        # schedule asks for bwd_chunks > 1)
+        # schedule asks for chunks > 1)
         self.chunk_poses = B.batch_plan_chunks(plan)
         self.plan_host = plan.pin_memory() if torch.cuda.is_available() else plan
         self.plan_dev = plan.to(dev)

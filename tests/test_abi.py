@@ -90,7 +90,7 @@ def test_batch_workspace_covers_the_adjoint_state(lib):
 
 
 def test_backward_chunks_of_a_plan(lib):
-    # host-only planning: bwd_chunks cuts the poses into contiguous,
+    # host-only planning: chunks cuts the poses into contiguous,
     # non-empty ranges where the running work first reaches c/n of the total
     import math
     import numpy as np

@@ -310,11 +310,13 @@ def test_pipelined_transfers_match_plain_run():
 
 
 @pytest.mark.parametrize("form", [0, 1])
-def test_backward_chunks_match_one_chunk(form):
-    # bwd_chunks = 4: dL/dimage uploaded range by range on another stream,
-    # each range's event releasing its blur transpose and adjoint march; the
-    # images and both gradients equal a one-chunk run bitwise (the chunks
-    # change the order of independent rays only), also for a pose-only call
+def test_pose_chunks_match_one_chunk(form):
+    # chunks = 4: dL/dimage uploaded range by range on another stream, each
+    # range's event releasing its blur transpose and adjoint march, and each
+    # range's images downloaded on a third stream from the forward's event
+    # for that range; the images and both gradients equal a one-chunk run
+    # bitwise (the chunks change the order of independent rays only), also
+    # for a pose-only call
     import torch
     from paper_2508_06768_gb300 import binding as B
     vol, poses, fans, prm = _workload(mode=0, count=9, seed=37)
@@ -331,20 +333,36 @@ def test_backward_chunks_match_one_chunk(form):
     evs = [torch.cuda.Event() for _ in range(4)]
     for e in evs:
         e.record(s)
+    done = [torch.cuda.Event() for _ in range(4)]
+    for e in done:
+        e.record(s)
     tr = B.TraceDesc()
     for c, e in enumerate(evs):
         tr.wait_chunk[c] = e.cuda_event
+    for c, e in enumerate(done):
+        tr.fwd_chunk_done[c] = e.cuda_event
+    down = torch.cuda.Stream()
+    img_h = torch.empty(total, dtype=torch.float32).pin_memory()
     G = torch.empty(total, dtype=torch.float32, device="cuda")
     for _ in range(2):
         G.fill_(float("nan"))        # a range used before its copy would poison the gradients
+        r4.images.fill_(float("nan"))
         up.wait_stream(s)
         with torch.cuda.stream(up):
             for c, (a, b) in enumerate(r4.chunk_ranges()):
                 G[a:b].copy_(G_h[a:b], non_blocking=True)
                 evs[c].record(up)
         r4.run(pd, G, stream=s, trace=tr)
+        # each range's images as soon as the forward has finished them (a
+        # download before that would carry the NaNs written above)
+        for c, (a, b) in enumerate(r4.chunk_ranges()):
+            down.wait_event(done[c])
+            with torch.cuda.stream(down):
+                img_h[a:b].copy_(r4.images[a:b], non_blocking=True)
         s.wait_stream(up)
+        s.wait_stream(down)
         torch.cuda.synchronize()
+        assert torch.equal(img_h, r1.images.cpu())
         assert torch.equal(r4.images, r1.images)
         assert torch.equal(r4.ray_valid, r1.ray_valid)
         assert torch.equal(r4.grad_vol, r1.grad_vol)

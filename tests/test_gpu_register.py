@@ -29,12 +29,13 @@ def test_recovers_perturbed_pose():
     e_r = np.degrees(np.abs(res.pose[3:] - pose[3:]))
     print("translation error %.3f -> %.3f mm, rotation %.3f -> %s deg, loss %.3e -> %.3e"
           % (e0_t, e_t, e0_r, np.round(e_r, 3), res.losses[0], res.losses[-1]))
-    # measured: 3.46 mm -> 0.014 mm, 2.4 deg -> (0.074, 0.003, 0.119) deg;
-    # the bounds keep a factor of two or more
+    # measured (reproducibly: the renderer and the envelope's smoothing are
+    # deterministic): 3.46 mm -> 0.023 mm, 2.4 deg -> (0.127, 0.005, 0.209)
+    # deg; the bounds keep a factor of two or more
     assert res.losses[-1] < 0.05 * res.losses[0]
     assert e_t < 0.02 * e0_t
     # the in-plane angle (about the elevation axis y) is pinned by the image;
     # tilt out of the plane and roll about the beam move a slice of this
     # nearly symmetric phantom only weakly, so they converge more slowly
     assert e_r[1] < 0.01 * e0_r
-    assert e_r.max() < 0.1 * e0_r
+    assert e_r.max() < 0.2 * e0_r
