@@ -309,8 +309,8 @@ def test_pipelined_transfers_match_plain_run():
         assert torch.equal(r.grad_poses.cpu(), ref[2])
 
 
-@pytest.mark.parametrize("form", [0, 1])
-def test_pose_chunks_match_one_chunk(form):
+@pytest.mark.parametrize("form,refine", [(0, 0), (1, 0), (0, 1)])
+def test_pose_chunks_match_one_chunk(form, refine):
     # chunks = 4: dL/dimage uploaded range by range on another stream, each
     # range's event releasing its blur transpose and adjoint march, and each
     # range's images downloaded on a third stream from the forward's event
@@ -320,6 +320,7 @@ def test_pose_chunks_match_one_chunk(form):
     import torch
     from paper_2508_06768_gb300 import binding as B
     vol, poses, fans, prm = _workload(mode=0, count=9, seed=37)
+    prm = prm.with_(refine=refine)   # with the refined pass the forward runs whole, the backward in ranges
     r1 = _renderer(vol, fans, prm, sched=B.ScheduleDesc(4, 6, 8, form, 1))
     r4 = _renderer(vol, fans, prm, sched=B.ScheduleDesc(4, 6, 8, form, 4))
     assert len(r4.chunk_ranges()) == 4 and r4.chunk_ranges()[-1][1] == r4.n_ray_samples
